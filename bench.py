@@ -1,0 +1,362 @@
+"""Benchmark: orbit-steps/s of many-orbit Euler-Maruyama on one GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch):
+stochastic Kuramoto, scalar-sigma layout, n = 8 / 32 / 128 with
+2^20 / 2^18 / 2^16 orbits, dt = 0.005, 10^4 Euler-Maruyama steps per orbit,
+a frame every 100 steps, Philox seed 0; FP32 with Kahan-compensated state.
+Per step: reload the parameters and initial states from device memory, then
+integrate all three problems over the full horizon (frames written to HBM).
+
+The JSON line carries: the device-timed value (inputs resident in HBM), an
+end-to-end value through the C ABI with pinned host buffers (host->device
+inputs and device->host frames inside the timed region), a roofline entry
+for the dominant kernel (the forward Euler-Maruyama kernel, bound by the
+SFU / special-function pipe), the same workload in FP64 on a 1000-step
+prefix of the horizon, and the CPU oracle timed on this host's cores on a
+bounded sample.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "kuramoto_n8_n32_n128_dt0.005_K1e4_stride100"
+CONFIGS = [  # (n, orbits per GPU)
+    (8, 1 << 20),
+    (32, 1 << 18),
+    (128, 1 << 16),
+]
+DT, STEPS, STRIDE, SEED = 0.005, 10000, 100, 0
+METRIC = "orbit-steps/sec"
+# SFU (special function unit) operations the method needs per oscillator-step
+# in the FP32 path: sin and cos of the phase, and per normal half of the
+# Box-Muller (log, sqrt, sin, cos).
+SFU_OPS_PER_OSC_STEP = 4
+SFU_PER_SM_PER_CLK = 16
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_sample(nthreads, budget_orbits):
+    """Oracle (pairwise Kuramoto drift, as it stands) on the first orbits of
+    each problem, full horizon.  Returns (orbit-steps/s over the workload mix,
+    description)."""
+    import numpy as np
+
+    import oracle
+    from paper_1908_03869_gb300 import inputs
+
+    t_total, units_total = 0.0, 0
+    desc = []
+    for (n, orbits), s in zip(CONFIGS, budget_orbits):
+        p, x0 = inputs.kuramoto(n, s, seed=1)
+        pb = oracle.make_problem("kuramoto", n, n, n + 2, DT, STEPS, STRIDE, SEED)
+        t0 = time.perf_counter()
+        oracle.integrate(pb, p.astype(np.float32).astype(np.float64), x0.astype(np.float32).astype(np.float64),
+                         frames=True, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        rate = s * STEPS / dt
+        # time the full per-GPU problem would take at this rate (workload mix)
+        t_total += orbits * STEPS / rate
+        units_total += orbits * STEPS
+        desc.append("n=%d: first %d orbits x %d steps in %.2fs" % (n, s, STEPS, dt))
+    return units_total / t_total, "; ".join(desc)
+
+
+def _sample_sizes(cores):
+    # about 3-10 s of CPU work per problem on `cores` threads
+    return [8 * cores, 2 * cores, max(1, cores // 4)]
+
+
+def run_reference(args):
+    ws, rank, _ = _dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    sizes = [max(1, s // 2) for s in _sample_sizes(cores)]
+    for _ in range(args.warmup):
+        _cpu_sample(cores, [1, 1, 1])
+    vals, times = [], []
+    desc = ""
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        v, desc = _cpu_sample(cores, sizes)
+        times.append(time.perf_counter() - t0)
+        vals.append(v)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "orbit-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "orbits_per_gpu": [o for _, o in CONFIGS]},
+        "cpu_baseline": {"value": value, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": "per step: " + desc + "; rate scaled to the workload's orbit mix"},
+        "e2e": {"value": value, "unit": "orbit-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import build as sdeb_build
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    ws, rank, local = _dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(sdeb_build.LIB_PATH):
+        sdeb_build.build()
+    if dist is not None:
+        dist.barrier()
+    sdeb.lib()
+
+    stream = torch.cuda.Stream()
+    dtype = torch.float32
+    its, dev_inputs, host_inputs = [], [], []
+    for n, orbits in CONFIGS:
+        p, x0 = inputs.kuramoto(n, orbits, seed=1 + rank)
+        pb = sdeb.Problem.make("kuramoto", n, orbits, DT, STEPS, STRIDE, SEED, "fp32", orbit_offset=rank * orbits)
+        its.append(Integrator(pb))
+        pt, xt = torch.tensor(p, dtype=dtype), torch.tensor(x0, dtype=dtype)
+        dev_inputs.append((pt.cuda(), xt.cuda()))
+        host_inputs.append((pt.pin_memory(), xt.pin_memory()))
+    units_per_step = sum(o * STEPS for _, o in CONFIGS)
+    osc_per_step = sum(n * o * STEPS for n, o in CONFIGS)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # 512 MiB > 129 MB L2
+
+    def one_step(kernel_events=None):
+        for i, it in enumerate(its):
+            it.set_params(*dev_inputs[i], stream=stream)
+            if kernel_events is not None:
+                kernel_events[i][0].record(stream)
+            it.integrate(stream=stream)
+            if kernel_events is not None:
+                kernel_events[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            one_step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM --------------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in CONFIGS]
+               for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)  # evict L2 between timed steps (outside the step's events)
+            step_ev[s][0].record(stream)
+            one_step(kern_ev[s])
+            step_ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    kern_ms = [[a.elapsed_time(b) for a, b in row] for row in kern_ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = units_per_step * ws * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (forward EM, FP32) --------------
+    kernel_s = sum(sum(r) for r in kern_ms) / 1e3
+    sfu_ops = SFU_OPS_PER_OSC_STEP * osc_per_step * args.steps
+    achieved = sfu_ops / kernel_s / 1e9
+    peak = SFU_PER_SM_PER_CLK * NUM_SMS * SM_MAX_MHZ * 1e6 / 1e9
+    per_launch_ms = {str(n): statistics.mean(r[i] for r in kern_ms) for i, (n, _) in enumerate(CONFIGS)}
+
+    # ---- end to end through the C ABI with pinned host buffers ----------
+    e2e = None
+    if not args.no_e2e:
+        host_frames = [torch.empty((it.nframes, it.pb.orbits, it.pb.n), dtype=dtype, pin_memory=True) for it in its]
+        h2d = sum(p.numel() * p.element_size() + x.numel() * x.element_size() for p, x in host_inputs)
+        d2h = sum(f.numel() * f.element_size() for f in host_frames)
+
+        def e2e_step():
+            for i, it in enumerate(its):
+                it.set_params(*host_inputs[i], stream=stream)
+                it.integrate(stream=stream)
+                it.frames(out=host_frames[i], stream=stream)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": units_per_step * ws * args.steps / e2e_s, "unit": "orbit-steps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        del host_frames
+
+    # ---- FP64 on a 1000-step prefix of the same problems -----------------
+    fp64 = None
+    if not args.no_fp64:
+        steps64 = 1000
+        t64, u64 = 0.0, 0
+        for n, orbits in CONFIGS:
+            p, x0 = inputs.kuramoto(n, orbits, seed=1 + rank)
+            pb = sdeb.Problem.make("kuramoto", n, orbits, DT, steps64, STRIDE, SEED, "fp64", orbit_offset=rank * orbits)
+            with Integrator(pb) as it64:
+                pt, xt = torch.tensor(p, device="cuda"), torch.tensor(x0, device="cuda")
+                it64.set_params(pt, xt, stream=stream)
+                it64.integrate(stream=stream)  # warm-up
+                it64.set_params(pt, xt, stream=stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                it64.integrate(stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t64 += a.elapsed_time(b) / 1e3
+                u64 += orbits * steps64
+        fp64 = {"value": u64 / t64, "unit": "orbit-steps/s", "steps_per_orbit": steps64,
+                "note": "same orbits, first 1000 of the 10^4 steps; cost per step is constant over the horizon"}
+
+    # ---- CPU oracle on this host's cores --------------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, desc = _cpu_sample(cores, _sample_sizes(cores))
+        cpu = {"value": v, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle",
+               "sample": desc + "; rate scaled to the workload's orbit mix"}
+
+    for it in its:
+        it.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "orbit-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp32 Kahan", "orbits_per_gpu": [o for _, o in CONFIGS],
+                       "n": [n for n, _ in CONFIGS], "dt": DT, "steps_per_orbit": STEPS, "stride": STRIDE,
+                       "l2": "flushed between steps (512 MiB write)", "parallelism": "orbits sharded, no collective"},
+            "oscillator_steps_per_sec": value * osc_per_step / units_per_step,
+            "wall_s": wall,
+            "per_launch_ms": per_launch_ms,
+            "roofline": {"bound": "alu", "pipe": "SFU (MUFU)", "achieved": achieved, "peak": peak,
+                         "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
+                         "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
+            "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": len(CONFIGS) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * sdeb.h -- C ABI of a GB300 (sm_103a) library that integrates many
+ * independent orbits of an Ito SDE system with fixed-step Euler-Maruyama.
+ *
+ * The method is the one of SODECL (Avramidis, Lalik, Akman, arXiv 1908.03869):
+ *   Eq. 1   dX_i = f_i(t, X, p) dt + sum_j g_ij(t, X, p) dW_j,
+ *           n states, m Wiener processes, d parameters (Sec. 1.1);
+ *   Eq. 2   X^{k+1}_i = X^k_i + f_i dt + sum_j g_ij sqrt(dt) N_j(0,1) (Sec. 2.1.1);
+ *   Eq. 3   N_j from uniforms by Box-Muller, uniforms from a counter-based
+ *           generator (Sec. 2.1.2);
+ *   Eq. 4   output every `stride` steps (Sec. 2.1.4);
+ *   Eq. 5/6 the stochastic Kuramoto model (Sec. 2.2.1);
+ *   Eq. 7   the Kuramoto order parameter (Sec. 2.3.1).
+ * The problem description mirrors the paper's arguments (Table 2: initial
+ * states, parameter sets, orbits, n, d, m, dt, time span, steps per output).
+ *
+ * Conventions (every entry point):
+ *   - Every call returns an sdeb_status; nothing throws across the ABI.
+ *     sdeb_last_error(ctx) gives a one-line description of the last failure
+ *     on that context.
+ *   - A context owns all of its device buffers.  Input pointers are copied
+ *     during the call (or, for device pointers, by stream-ordered copies
+ *     enqueued on the given stream) and never retained.
+ *   - Element type of every state / parameter / frame / gradient buffer is
+ *     the context precision: float for SDEB_FP32_KAHAN, double for SDEB_FP64.
+ *   - Row-major layouts: params [orbits][d] (or [d] with
+ *     SDEB_FLAG_SHARED_PARAMS), states [orbits][n], frames [F][orbits][n]
+ *     with F = steps / stride + 1, frame f = state at step f * stride.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Compute calls are asynchronous on that stream.
+ *   - No entry point prints, aborts or falls back to the CPU.  If the CUDA
+ *     runtime or the device is unavailable a call returns SDEB_ECUDA.
+ *
+ * Noise (reading of Sec. 2.1.2, which names Random123 but no generator or
+ * layout): Philox4x32-10 (Salmon et al., SC'11) with key = (seed lo32,
+ * seed hi32) and counter = (step k, noise block b = j / 4, global orbit index,
+ * stream 0).  Words (w0, w1) of a block give N_{4b} (cos branch) and
+ * N_{4b+1} (sin branch) with U1 = (w0 + 1/2) 2^-32 setting the radius and
+ * U2 = (w1 + 1/2) 2^-32 the angle; (w2, w3) give N_{4b+2}, N_{4b+3}.  Words
+ * past m are discarded.  Nothing is stored: any draw can be regenerated.
+ */
+#ifndef SDEB_H
+#define SDEB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SDEB_API __attribute__((visibility("default")))
+#else
+#define SDEB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SDEB_OK = 0,
+    SDEB_EINVAL = 1,        /* an argument is out of range or inconsistent */
+    SDEB_ENOMEM = 2,        /* a device or host allocation failed */
+    SDEB_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SDEB_ETIMEOUT = 4,      /* a bounded device wait gave up */
+    SDEB_ESTATE = 5,        /* call order violated (e.g. read before integrate) */
+    SDEB_EUNSUPPORTED = 6,  /* valid request the library does not implement */
+    SDEB_ENONFINITE = 7     /* some orbit left the finite range (see sdeb_orbit_flags) */
+} sdeb_status;
+
+/* Models (drift f and diffusion g of Eq. 1). */
+enum {
+    /* Kuramoto, Eq. 5/6 with one noise strength: n = m, d = n + 2,
+     * p = (K, sigma, omega_1..omega_n), f_i = omega_i + K/n sum_j sin(x_j - x_i),
+     * g_ij = sigma delta_ij. */
+    SDEB_KURAMOTO = 1,
+    /* Kuramoto in the paper's parameter layout (Eq. 5 footnote): n = m,
+     * d = 2n + 1, p = (K, omega_1..omega_n, p_1..p_n), g_ij = p_i delta_ij. */
+    SDEB_KURAMOTO_PAPER = 2,
+    /* FitzHugh-Nagumo network of u = n/2 units, x = (v_1..v_u, w_1..w_u),
+     * m = u, d = 6, p = (a, b, eps, I, c, sigma):
+     * dv_i = (v_i - v_i^3/3 - w_i + I + c mean(v) - c v_i) dt + sigma v_i dW_i,
+     * dw_i = eps (v_i + a - b w_i) dt. */
+    SDEB_FHN_NET = 3,
+    /* Ornstein-Uhlenbeck dX_i = -theta X_i dt + sigma dW_i, m = n, p = (theta, sigma). */
+    SDEB_OU = 4,
+    /* Geometric Brownian motion dX_i = mu X_i dt + sigma X_i dW_i, m = n, p = (mu, sigma). */
+    SDEB_GBM = 5,
+    /* Linear ODE (g = 0) dx_i = -theta x_i dt, m = 0, p = (theta). */
+    SDEB_LINEAR_ODE = 6
+};
+
+/* Precision.  FP32_KAHAN: float state with a Kahan compensation word per
+ * state component, float arithmetic, FP64 time variable.  FP64: double
+ * everywhere. */
+enum { SDEB_FP32_KAHAN = 0, SDEB_FP64 = 1 };
+
+/* Problem flags. */
+enum {
+    SDEB_FLAG_SHARED_PARAMS = 1u, /* one parameter vector [d] for every orbit */
+    SDEB_FLAG_NO_FRAMES = 2u      /* keep only the final state (no frame buffer) */
+};
+
+typedef struct {
+    int32_t model;        /* SDEB_KURAMOTO ... SDEB_LINEAR_ODE */
+    int32_t n, m, d;      /* states, Wiener processes, parameters (must match the model) */
+    int64_t orbits;       /* orbits in this context, >= 1 */
+    double t0, dt;        /* initial time; step > 0 and finite */
+    int64_t steps;        /* K >= 0, K < 2^32 */
+    int64_t stride;       /* output every `stride` steps, >= 1 */
+    uint64_t seed;        /* Philox key */
+    int32_t precision;    /* SDEB_FP32_KAHAN or SDEB_FP64 */
+    int32_t ckpt_every;   /* > 0: keep checkpoints every ckpt_every steps (needed by sdeb_grad) */
+    uint32_t flags;       /* SDEB_FLAG_* */
+    uint32_t reserved;    /* must be 0 */
+    int64_t orbit_offset; /* global index of orbit 0 (Philox keying); offset + orbits <= 2^32 */
+} sdeb_problem;
+
+typedef struct sdeb_ctx sdeb_ctx;   /* opaque, library-owned */
+
+/* Validate the problem and allocate the context's device buffers on the
+ * current CUDA device.  On failure *out is NULL and the status says why
+ * (EINVAL before any CUDA call; ENOMEM / ECUDA afterwards). */
+SDEB_API sdeb_status sdeb_create(const sdeb_problem *pb, sdeb_ctx **out);
+
+/* Free the context and its device buffers (synchronises the device first).
+ * NULL is accepted. */
+SDEB_API void sdeb_destroy(sdeb_ctx *ctx);
+
+/* Load parameter sets and initial states (Table 2 arguments "params" and
+ * "initx").  params: [orbits][d] (or [d] when shared); x0: [orbits][n];
+ * element type = context precision.  on_device = 0: host pointers, copied
+ * before return; 1: device pointers, copied on `stream`.  Resets the step
+ * counter to 0 and writes frame 0. */
+SDEB_API sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0,
+                            int32_t on_device, void *stream);
+
+/* Integrate all orbits over the whole horizon k = 0..steps (Eq. 2), writing
+ * frames every `stride` steps.  Requires sdeb_set_params.  Asynchronous. */
+SDEB_API sdeb_status sdeb_integrate(sdeb_ctx *ctx, void *stream);
+
+/* Integrate steps [k_begin, k_end) only; k_begin must equal the context's
+ * current step (state and compensation carry over, so 0..K equals
+ * 0..j + j..K bit for bit). */
+SDEB_API sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, void *stream);
+
+/* Copy frames [frame_begin, frame_begin + frame_count) into dst, layout
+ * [frame_count][orbits][n]; dst_bytes must equal that size exactly.  Frames
+ * past the current step are ESTATE.  dst_on_device selects device/host dst
+ * (host copies complete before return). */
+SDEB_API sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int64_t frame_begin,
+                             int64_t frame_count, int32_t dst_on_device, void *stream);
+
+/* Copy the current state [orbits][n] into dst (dst_bytes exact). */
+SDEB_API sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t dst_on_device,
+                            void *stream);
+
+/* Pathwise gradient by the discrete adjoint of Eq. 2 (checkpointed
+ * recompute, Philox noise regenerated).  Requires ckpt_every > 0 and a
+ * completed integration to k = steps.  All pointers are device pointers of
+ * the context precision:
+ *   dL_dxK [orbits][n] (input),
+ *   dL_dp  [orbits][d] per orbit, or [d] summed over orbits when the
+ *          parameters are shared (output),
+ *   dL_dx0 [orbits][n] or NULL (output).
+ * Supported models: SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER (others: EUNSUPPORTED). */
+SDEB_API sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_dx0, void *stream);
+
+/* Per-orbit status bits after the last integration: bit 0 = a state
+ * component is not finite.  dst: host [orbits]; synchronises `stream`. */
+SDEB_API sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream);
+
+/* Device pointer to the frame buffer ([F][orbits][n], context precision)
+ * and its size, for zero-copy use; *ptr = NULL with SDEB_FLAG_NO_FRAMES.
+ * The pointer stays valid until sdeb_destroy. */
+SDEB_API sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *bytes);
+
+SDEB_API const char *sdeb_last_error(const sdeb_ctx *ctx);
+SDEB_API const char *sdeb_status_string(sdeb_status s);
+
+/* ---- Stand-alone kernels of the path (device pointers) ------------------ */
+
+/* Raw Philox4x32-10 words of the Wiener stream layout: out[k][b][o][4] for
+ * k in [k0, k0+nk), b in [b0, b0+nb), o in [o0, o0+no), counter stream word
+ * `stream_id` (Sec. 2.1.2 reading above).  out: device uint32. */
+SDEB_API sdeb_status sdeb_philox_fill(uint64_t seed, uint32_t k0, int64_t nk, uint32_t b0, int64_t nb,
+                             uint32_t o0, int64_t no, uint32_t stream_id, uint32_t *out,
+                             void *stream);
+
+/* The m standard normals of Eq. 3 for steps [k0, k0+nk) and orbits
+ * [o0, o0+no): out[k][o][m] in `precision` (device pointer). */
+SDEB_API sdeb_status sdeb_normals_fill(uint64_t seed, uint32_t k0, int64_t nk, uint32_t o0, int64_t no,
+                              int32_t m, int32_t precision, void *out, void *stream);
+
+/* Kuramoto order parameter, Eq. 7: r[o] = |(1/n) sum_j exp(i theta[o][j])|
+ * and, if dr != NULL, dr[o][l] = d r[o] / d theta[o][l] (zero where r = 0).
+ * theta [orbits][n], r [orbits], dr [orbits][n]; device pointers in
+ * `precision`. */
+SDEB_API sdeb_status sdeb_order_param(const void *theta, int64_t orbits, int32_t n, int32_t precision,
+                             void *r, void *dr, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDEB_H */

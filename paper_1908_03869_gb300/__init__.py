@@ -1,0 +1,202 @@
+"""Many-orbit Euler-Maruyama integration of Ito SDEs on GB300 (sm_103a).
+
+Thin ctypes binding of the C ABI in include/sdeb.h: every ``sdeb_*``
+function here has the C entry point's name and arguments and only marshals
+them; all work runs in the CUDA library ``_build/libsdeb.so``.  A missing
+library is an error (there is no CPU fallback).  PyTorch is used only for
+device memory and streams (``torch.Tensor.data_ptr()`` / ``cuda_stream``).
+
+Build the library with ``paper_1908_03869_gb300.build.build()`` (or
+``__graft_entry__.build()``).
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "SdebError", "Problem", "lib", "library_path",
+    "SDEB_OK", "SDEB_EINVAL", "SDEB_ENOMEM", "SDEB_ECUDA", "SDEB_ETIMEOUT", "SDEB_ESTATE",
+    "SDEB_EUNSUPPORTED", "SDEB_ENONFINITE",
+    "SDEB_KURAMOTO", "SDEB_KURAMOTO_PAPER", "SDEB_FHN_NET", "SDEB_OU", "SDEB_GBM", "SDEB_LINEAR_ODE",
+    "SDEB_FP32_KAHAN", "SDEB_FP64", "SDEB_FLAG_SHARED_PARAMS", "SDEB_FLAG_NO_FRAMES",
+    "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
+    "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
+    "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
+    "model_shape", "EXPORTED_SYMBOLS",
+]
+
+SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
+SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER, SDEB_FHN_NET, SDEB_OU, SDEB_GBM, SDEB_LINEAR_ODE = range(1, 7)
+SDEB_FP32_KAHAN, SDEB_FP64 = 0, 1
+SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES = 1, 2
+
+MODEL_IDS = {
+    "kuramoto": SDEB_KURAMOTO, "kuramoto_paper": SDEB_KURAMOTO_PAPER, "fhn_net": SDEB_FHN_NET,
+    "ou": SDEB_OU, "gbm": SDEB_GBM, "linear_ode": SDEB_LINEAR_ODE,
+}
+PRECISIONS = {"fp32": SDEB_FP32_KAHAN, "fp64": SDEB_FP64}
+
+
+def model_shape(model, n):
+    """(m, d) of a model for n states (the rule sdeb_create enforces)."""
+    model = MODEL_IDS.get(model, model)
+    return {
+        SDEB_KURAMOTO: (n, n + 2), SDEB_KURAMOTO_PAPER: (n, 2 * n + 1), SDEB_FHN_NET: (n // 2, 6),
+        SDEB_OU: (n, 2), SDEB_GBM: (n, 2), SDEB_LINEAR_ODE: (0, 1),
+    }[model]
+
+
+class Problem(ctypes.Structure):
+    """sdeb_problem (include/sdeb.h)."""
+    _fields_ = [
+        ("model", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("d", ctypes.c_int32),
+        ("orbits", ctypes.c_int64), ("t0", ctypes.c_double), ("dt", ctypes.c_double),
+        ("steps", ctypes.c_int64), ("stride", ctypes.c_int64), ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int32), ("ckpt_every", ctypes.c_int32), ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32), ("orbit_offset", ctypes.c_int64),
+    ]
+
+    @classmethod
+    def make(cls, model, n, orbits, dt, steps, stride=1, seed=0, precision="fp32", t0=0.0, ckpt_every=0,
+             shared_params=False, no_frames=False, orbit_offset=0, m=None, d=None):
+        mid = MODEL_IDS.get(model, model)
+        m0, d0 = model_shape(mid, n) if mid in MODEL_IDS.values() else (0, 0)
+        flags = (SDEB_FLAG_SHARED_PARAMS if shared_params else 0) | (SDEB_FLAG_NO_FRAMES if no_frames else 0)
+        return cls(mid, n, m0 if m is None else m, d0 if d is None else d, orbits, t0, dt, steps, stride,
+                   seed & 0xFFFFFFFFFFFFFFFF, PRECISIONS.get(precision, precision), ckpt_every, flags, 0,
+                   orbit_offset)
+
+
+class SdebError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (status %d: %s)" % (message, status, _STATUS_NAMES.get(status, "?")))
+        self.status = status
+
+
+_STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE",
+                 6: "EUNSUPPORTED", 7: "ENONFINITE"}
+
+_P = ctypes.c_void_p
+_ST = ctypes.c_int
+_SIGS = {
+    "sdeb_create": (_ST, [ctypes.POINTER(Problem), ctypes.POINTER(_P)]),
+    "sdeb_destroy": (None, [_P]),
+    "sdeb_set_params": (_ST, [_P, _P, _P, ctypes.c_int32, _P]),
+    "sdeb_integrate": (_ST, [_P, _P]),
+    "sdeb_integrate_range": (_ST, [_P, ctypes.c_int64, ctypes.c_int64, _P]),
+    "sdeb_read_orbits": (_ST, [_P, _P, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P]),
+    "sdeb_read_final": (_ST, [_P, _P, ctypes.c_size_t, ctypes.c_int32, _P]),
+    "sdeb_grad": (_ST, [_P, _P, _P, _P, _P]),
+    "sdeb_orbit_flags": (_ST, [_P, _P, _P]),
+    "sdeb_frames_device_ptr": (_ST, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),
+    "sdeb_last_error": (ctypes.c_char_p, [_P]),
+    "sdeb_status_string": (ctypes.c_char_p, [_ST]),
+    "sdeb_philox_fill": (_ST, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64,
+                               ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint32, _P, _P]),
+    "sdeb_normals_fill": (_ST, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64,
+                                ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "sdeb_order_param": (_ST, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+}
+EXPORTED_SYMBOLS = tuple(_SIGS)
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB_PATH
+
+
+def lib():
+    """Load libsdeb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError("CUDA library %s is missing; run paper_1908_03869_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != SDEB_OK:
+        msg = lib().sdeb_last_error(ctx)
+        raise SdebError(status, msg.decode() if msg else "")
+
+
+def _stream(stream):
+    """Accept None, an int handle, or a torch.cuda.Stream."""
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def sdeb_create(problem):
+    ctx = _P()
+    _check(lib().sdeb_create(ctypes.byref(problem), ctypes.byref(ctx)))
+    return ctx
+
+
+def sdeb_destroy(ctx):
+    lib().sdeb_destroy(ctx)
+
+
+def sdeb_set_params(ctx, params, x0, on_device, stream=None):
+    _check(lib().sdeb_set_params(ctx, params, x0, int(on_device), _stream(stream)), ctx)
+
+
+def sdeb_integrate(ctx, stream=None):
+    _check(lib().sdeb_integrate(ctx, _stream(stream)), ctx)
+
+
+def sdeb_integrate_range(ctx, k_begin, k_end, stream=None):
+    _check(lib().sdeb_integrate_range(ctx, k_begin, k_end, _stream(stream)), ctx)
+
+
+def sdeb_read_orbits(ctx, dst, dst_bytes, frame_begin, frame_count, dst_on_device, stream=None):
+    _check(lib().sdeb_read_orbits(ctx, dst, dst_bytes, frame_begin, frame_count, int(dst_on_device),
+                                  _stream(stream)), ctx)
+
+
+def sdeb_read_final(ctx, dst, dst_bytes, dst_on_device, stream=None):
+    _check(lib().sdeb_read_final(ctx, dst, dst_bytes, int(dst_on_device), _stream(stream)), ctx)
+
+
+def sdeb_grad(ctx, dL_dxK, dL_dp, dL_dx0=None, stream=None):
+    _check(lib().sdeb_grad(ctx, dL_dxK, dL_dp, dL_dx0, _stream(stream)), ctx)
+
+
+def sdeb_orbit_flags(ctx, dst, stream=None):
+    _check(lib().sdeb_orbit_flags(ctx, dst, _stream(stream)), ctx)
+
+
+def sdeb_frames_device_ptr(ctx):
+    p, b = _P(), ctypes.c_size_t()
+    _check(lib().sdeb_frames_device_ptr(ctx, ctypes.byref(p), ctypes.byref(b)), ctx)
+    return p.value, b.value
+
+
+def sdeb_last_error(ctx=None):
+    s = lib().sdeb_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def sdeb_status_string(status):
+    return lib().sdeb_status_string(status).decode()
+
+
+def sdeb_philox_fill(seed, k0, nk, b0, nb, o0, no, stream_id, out, stream=None):
+    _check(lib().sdeb_philox_fill(seed, k0, nk, b0, nb, o0, no, stream_id, out, _stream(stream)))
+
+
+def sdeb_normals_fill(seed, k0, nk, o0, no, m, precision, out, stream=None):
+    _check(lib().sdeb_normals_fill(seed, k0, nk, o0, no, m, precision, out, _stream(stream)))
+
+
+def sdeb_order_param(theta, orbits, n, precision, r, dr=None, stream=None):
+    _check(lib().sdeb_order_param(theta, orbits, n, precision, r, dr, _stream(stream)))

@@ -1,0 +1,228 @@
+// Forward Euler-Maruyama kernel (Eq. 2) for the lane-group layout, with the
+// Philox draw, Box-Muller, drift, diffusion, compensated update and strided
+// output fused into one pass over the horizon.  Included by the translation
+// units that instantiate it for a set of models, precisions and layouts.
+#pragma once
+
+#include <type_traits>
+
+#include "em_internal.h"
+#include "em_models.cuh"
+
+namespace sdeb {
+
+constexpr int kForwardBlock = 128;
+
+// Loads / stores of a lane's units: component c of unit j is row[c*units + j].
+// Full, 16-byte aligned runs use 16-byte vector accesses.
+template <typename Real, int U, int P>
+__device__ __forceinline__ void load_units(const Real *row, int units, int u0, Real (&v)[U][P]) {
+    constexpr int kVec = 16 / sizeof(Real);
+#pragma unroll
+    for (int c = 0; c < U; ++c) {
+        const Real *src = row + (int64_t)c * units + u0;
+        if (P % kVec == 0 && u0 + P <= units && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+#pragma unroll
+            for (int i = 0; i < P; i += kVec) {
+                if (sizeof(Real) == 4) {
+                    float4 q = *reinterpret_cast<const float4 *>(src + i);
+                    v[c][i] = q.x; v[c][i + 1] = q.y; v[c][i + 2] = q.z; v[c][i + 3] = q.w;
+                } else {
+                    double2 q = *reinterpret_cast<const double2 *>(src + i);
+                    v[c][i] = q.x; v[c][i + 1] = q.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) v[c][i] = (u0 + i < units) ? src[i] : Real(0);
+        }
+    }
+}
+
+template <typename Real, int U, int P>
+__device__ __forceinline__ void store_units(Real *row, int units, int u0, const Real (&v)[U][P]) {
+    constexpr int kVec = 16 / sizeof(Real);
+#pragma unroll
+    for (int c = 0; c < U; ++c) {
+        Real *dst = row + (int64_t)c * units + u0;
+        if (P % kVec == 0 && u0 + P <= units && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+            for (int i = 0; i < P; i += kVec) {
+                if (sizeof(Real) == 4) {
+                    *reinterpret_cast<float4 *>(dst + i) =
+                        make_float4(v[c][i], v[c][i + 1], v[c][i + 2], v[c][i + 3]);
+                } else {
+                    *reinterpret_cast<double2 *>(dst + i) = make_double2(v[c][i], v[c][i + 1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (u0 + i < units) dst[i] = v[c][i];
+        }
+    }
+}
+
+// One step of Eq. 2 for the lane's units: coupling sums over the group, then
+// per noise block one Philox call (counter (k, block, orbit, 0)), Box-Muller,
+// and the compensated update of every unit of the block.  Every unit's
+// increment reads only the old state (synchronous update).
+template <class M, typename Real, int G, int P>
+__device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], uint32_t k,
+                                        uint32_t orbit, int u0, int units, const PhiloxKeys &keys) {
+    constexpr int NRA = M::NR > 0 ? M::NR : 1;
+    Real red[NRA];
+    model.prepare(x, cp, u0, units, red);
+#pragma unroll
+    for (int r = 0; r < M::NR; ++r) red[r] = group_sum<G>(red[r]);
+    constexpr int NB = (P + 3) / 4;
+#pragma unroll
+    for (int blk = 0; blk < NB; ++blk) {
+        Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+        if (M::kNoise) {
+            uint32_t b = (uint32_t)(u0 >> 2) + (uint32_t)blk;
+            U32x4 w = philox4x32_10(k, b, orbit, 0u, keys);
+            box_muller<Real>(w.x, w.y, z[0], z[1]);
+            if (P - 4 * blk > 2) box_muller<Real>(w.z, w.w, z[2], z[3]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = 4 * blk + q;
+            if (i < P) {
+                Real inc[M::U];
+                model.incr(i, x, red, z[q], inc);
+#pragma unroll
+                for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
+            }
+        }
+    }
+}
+
+template <class M, typename Real, int G, int P>
+__global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const ForwardArgs a) {
+    constexpr int U = M::U;
+    constexpr bool kKahan = std::is_same<Real, float>::value;
+    static_assert(G == 1 || P % 4 == 0, "multi-lane orbits need whole noise blocks per lane");
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t orbit = tid / G;
+    const int lig = (int)(tid & (G - 1));
+    const bool active = orbit < a.orbits;
+    const int64_t o = active ? orbit : a.orbits - 1;
+    const int u0 = lig * P;
+    const int units = a.units;
+    const int64_t n = a.n;
+
+    M model;
+    model.load(static_cast<const Real *>(a.params) + o * a.param_stride, u0, units, (Real)a.dt,
+               (Real)sqrt(a.dt));
+
+    Real *xrow = static_cast<Real *>(a.x) + o * n;
+    Real x[U][P], cp[U][P];
+    load_units<Real, U, P>(xrow, units, u0, x);
+    if constexpr (kKahan) {
+        load_units<float, U, P>(a.comp + o * n, units, u0, cp);
+    } else {
+#pragma unroll
+        for (int c = 0; c < U; ++c)
+#pragma unroll
+            for (int i = 0; i < P; ++i) cp[c][i] = Real(0);
+    }
+
+    const uint32_t gorb = a.orbit_offset + (uint32_t)o;
+    Real *frames = static_cast<Real *>(a.frames);
+    Real *ckpt = static_cast<Real *>(a.ckpt);
+    uint32_t to_frame = a.stride - (a.k_begin % a.stride);
+    uint32_t to_ckpt = a.ckpt_every ? a.ckpt_every - (a.k_begin % a.ckpt_every) : 0u;
+
+    for (uint32_t k = a.k_begin; k < a.k_end; ++k) {
+        em_step<M, Real, G, P>(model, x, cp, k, gorb, u0, units, a.keys);
+        if (frames != nullptr && --to_frame == 0) {
+            to_frame = a.stride;
+            const int64_t f = (int64_t)((k + 1) / a.stride);
+            if (active) store_units<Real, U, P>(frames + (f * a.orbits + o) * n, units, u0, x);
+        }
+        if (ckpt != nullptr && --to_ckpt == 0) {
+            to_ckpt = a.ckpt_every;
+            const int64_t c = (int64_t)((k + 1) / a.ckpt_every);
+            if (active) {
+                store_units<Real, U, P>(ckpt + (c * a.orbits + o) * n, units, u0, x);
+                if constexpr (kKahan)
+                    store_units<float, U, P>(a.ckpt_comp + (c * a.orbits + o) * n, units, u0, cp);
+            }
+        }
+    }
+
+    // final state, compensation and the non-finite flag
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < U; ++c)
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            if (u0 + i < units && !isfinite(x[c][i])) bad = true;
+    const unsigned ballot = __ballot_sync(0xffffffffu, bad);
+    const int lane = threadIdx.x & 31;
+    unsigned group_bits;
+    if constexpr (G == 32) {
+        group_bits = ballot;
+    } else {
+        group_bits = (ballot >> (lane & ~(G - 1))) & ((1u << G) - 1u);
+    }
+    if (active) {
+        store_units<Real, U, P>(xrow, units, u0, x);
+        if constexpr (kKahan) store_units<float, U, P>(a.comp + o * n, units, u0, cp);
+        if (lig == 0) a.flags[o] = group_bits ? 1u : 0u;
+    }
+}
+
+template <template <typename, int> class MF, typename Real, int G, int P>
+cudaError_t launch_forward_layout(const ForwardArgs &a, cudaStream_t s) {
+    const int64_t threads = a.orbits * G;
+    const int64_t grid = (threads + kForwardBlock - 1) / kForwardBlock;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    em_forward_kernel<MF<Real, P>, Real, G, P><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define SDEB_FORWARD_LAYOUT(G_, P_) \
+    if (l.G == (G_) && l.P == (P_)) return launch_forward_layout<MF, Real, G_, P_>(a, s);
+
+// The layouts default_layout() can return.
+template <template <typename, int> class MF, typename Real>
+cudaError_t dispatch_default_layouts(const ForwardArgs &a, Layout l, cudaStream_t s) {
+    SDEB_FORWARD_LAYOUT(1, 1)
+    SDEB_FORWARD_LAYOUT(1, 2)
+    SDEB_FORWARD_LAYOUT(1, 4)
+    SDEB_FORWARD_LAYOUT(1, 8)
+    SDEB_FORWARD_LAYOUT(2, 8)
+    SDEB_FORWARD_LAYOUT(4, 8)
+    SDEB_FORWARD_LAYOUT(8, 8)
+    SDEB_FORWARD_LAYOUT(16, 8)
+    SDEB_FORWARD_LAYOUT(32, 8)
+    return cudaErrorNotSupported;
+}
+
+// Extra layouts tried by the layout tuner for the phase models.
+template <template <typename, int> class MF, typename Real>
+cudaError_t dispatch_tuning_layouts(const ForwardArgs &a, Layout l, cudaStream_t s) {
+    SDEB_FORWARD_LAYOUT(2, 4)
+    SDEB_FORWARD_LAYOUT(4, 4)
+    SDEB_FORWARD_LAYOUT(8, 4)
+    SDEB_FORWARD_LAYOUT(16, 4)
+    SDEB_FORWARD_LAYOUT(32, 4)
+    SDEB_FORWARD_LAYOUT(4, 16)
+    SDEB_FORWARD_LAYOUT(8, 16)
+    return dispatch_default_layouts<MF, Real>(a, l, s);
+}
+
+template <typename Real, int P>
+using KuramotoScalarLane = KuramotoLane<Real, P, false>;
+template <typename Real, int P>
+using KuramotoPaperLane = KuramotoLane<Real, P, true>;
+template <typename Real, int P>
+using OuLane = ScalarLane<Real, P, 0>;
+template <typename Real, int P>
+using GbmLane = ScalarLane<Real, P, 1>;
+template <typename Real, int P>
+using LinearLane = ScalarLane<Real, P, 2>;
+
+}  // namespace sdeb

@@ -1,0 +1,142 @@
+// Drift / diffusion functors of Eq. 1 for the lane-group layout.
+//
+// An orbit is integrated by G consecutive lanes; lane g owns the P "units"
+// u0 = g P .. u0 + P - 1.  A unit is one Wiener channel with its U state
+// components (U = 1 for the phase / scalar models, U = 2 for a
+// FitzHugh-Nagumo unit (v, w)).  Units at or past `units` are padding: they
+// hold zeros, add nothing to the coupling sums and are never stored.
+//
+// Each functor provides
+//   load(p, u0, units, dt, sqdt)      parameters of the orbit into registers
+//   prepare(x, cp, u0, units, red)    per-lane partial coupling sums (and any
+//                                     per-unit value reused by incr); cp is
+//                                     the Kahan compensation (zero in FP64)
+//   incr(i, x, red, N, inc)           the Eq. 2 increment f dt + g sqrt(dt) N
+//                                     of unit i's components, after red has
+//                                     been summed over the G lanes.
+// State component c of unit j lives at x[c * units + j] in the orbit's row.
+#pragma once
+
+#include "em_device.cuh"
+
+namespace sdeb {
+
+// Kuramoto, Eq. 5/6, drift in its mean-field form: with C = sum_j cos x_j and
+// S = sum_j sin x_j, sum_j sin(x_j - x_i) = S cos x_i - C sin x_i.
+// PAPER = false: p = (K, sigma, omega_1..omega_n); true: p = (K, omega, p_1..p_n).
+template <typename Real, int P, bool PAPER>
+struct KuramotoLane {
+    static constexpr int U = 1;
+    static constexpr int NR = 2;
+    static constexpr bool kNoise = true;
+    Real omega[P];
+    Real gsq[PAPER ? P : 1];  // noise strength times sqrt(dt)
+    Real kn;                  // K / n
+    Real dt;
+    Real sn[P], cs[P];
+
+    __device__ __forceinline__ void load(const Real *p, int u0, int units, Real dt_, Real sqdt) {
+        dt = dt_;
+        kn = p[0] / (Real)units;
+        if (!PAPER) gsq[0] = p[1] * sqdt;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            int j = u0 + i;
+            bool ok = j < units;
+            omega[i] = ok ? p[(PAPER ? 1 : 2) + j] : Real(0);
+            if (PAPER) gsq[i] = ok ? p[1 + units + j] * sqdt : Real(0);
+        }
+    }
+
+    __device__ __forceinline__ void prepare(const Real (&x)[U][P], const Real (&cp)[U][P], int u0, int units,
+                                            Real (&red)[NR]) {
+        Real C = 0, S = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            sincos_phase(x[0][i], cp[0][i], sn[i], cs[i]);
+            if (u0 + i < units) {
+                C += cs[i];
+                S += sn[i];
+            }
+        }
+        red[0] = C;
+        red[1] = S;
+    }
+
+    __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&red)[NR], Real N,
+                                         Real (&inc)[U]) const {
+        (void)x;
+        Real coupling = red[1] * cs[i] - red[0] * sn[i];
+        Real f = omega[i] + kn * coupling;
+        inc[0] = f * dt + gsq[PAPER ? i : 0] * N;
+    }
+};
+
+// FitzHugh-Nagumo network: unit j has v_j = x[j], w_j = x[units + j];
+// p = (a, b, eps, I, c, sigma); multiplicative noise sigma v_j dW_j on v only.
+template <typename Real, int P>
+struct FhnLane {
+    static constexpr int U = 2;
+    static constexpr int NR = 1;
+    static constexpr bool kNoise = true;
+    Real a, b, eps, I, c, gsq, dt, inv_units;
+
+    __device__ __forceinline__ void load(const Real *p, int, int units, Real dt_, Real sqdt) {
+        a = p[0];
+        b = p[1];
+        eps = p[2];
+        I = p[3];
+        c = p[4];
+        gsq = p[5] * sqdt;
+        dt = dt_;
+        inv_units = Real(1) / (Real)units;
+    }
+
+    __device__ __forceinline__ void prepare(const Real (&x)[U][P], const Real (&)[U][P], int u0, int units,
+                                            Real (&red)[NR]) {
+        Real sv = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            if (u0 + i < units) sv += x[0][i];
+        red[0] = sv;
+    }
+
+    __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&red)[NR], Real N,
+                                         Real (&inc)[U]) const {
+        Real v = x[0][i], w = x[1][i];
+        Real mean_v = red[0] * inv_units;
+        Real fv = v - v * v * v * Real(1.0 / 3.0) - w + I + c * mean_v - c * v;
+        Real fw = eps * (v + a - b * w);
+        inc[0] = fv * dt + gsq * v * N;
+        inc[1] = fw * dt;
+    }
+};
+
+// Ornstein-Uhlenbeck (KIND 0), geometric Brownian motion (KIND 1) and the
+// linear ODE (KIND 2, no noise): componentwise, no coupling.
+template <typename Real, int P, int KIND>
+struct ScalarLane {
+    static constexpr int U = 1;
+    static constexpr int NR = 0;
+    static constexpr bool kNoise = KIND != 2;
+    Real rate, gsq, dt;
+
+    __device__ __forceinline__ void load(const Real *p, int, int, Real dt_, Real sqdt) {
+        rate = p[0];
+        gsq = KIND == 2 ? Real(0) : p[1] * sqdt;
+        dt = dt_;
+    }
+
+    __device__ __forceinline__ void prepare(const Real (&)[U][P], const Real (&)[U][P], int, int,
+                                            Real (&)[NR > 0 ? NR : 1]) {}
+
+    __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&)[NR > 0 ? NR : 1],
+                                         Real N, Real (&inc)[U]) const {
+        Real xi = x[0][i];
+        if (KIND == 0) inc[0] = -rate * xi * dt + gsq * N;
+        if (KIND == 1) inc[0] = rate * xi * dt + gsq * xi * N;
+        if (KIND == 2) inc[0] = -rate * xi * dt;
+    }
+};
+
+}  // namespace sdeb

@@ -1,0 +1,406 @@
+// C ABI of the library (declared in include/sdeb.h): argument validation,
+// device buffers owned by the context, the call-order state machine and the
+// kernel launches.  Every function returns a status; nothing throws.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "em_internal.h"
+#include "sdeb.h"
+
+using namespace sdeb;
+
+struct sdeb_ctx {
+    sdeb_problem pb;
+    int32_t units = 0;
+    size_t elem = 0;          // 4 or 8
+    int device = 0;
+    Layout layout{1, 1};
+    void *d_params = nullptr;
+    size_t params_bytes = 0;
+    void *d_x = nullptr;
+    float *d_comp = nullptr;
+    void *d_frames = nullptr;
+    int64_t nframes = 0;
+    void *d_ckpt = nullptr;
+    float *d_ckpt_comp = nullptr;
+    int64_t nckpt = 0;
+    uint8_t *d_flags = nullptr;
+    bool params_set = false;
+    int64_t k_current = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sdeb_status fail(sdeb_ctx *ctx, sdeb_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    g_last_error = buf;
+    return s;
+}
+
+sdeb_status cuda_fail(sdeb_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(ctx, SDEB_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(ctx, SDEB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+bool model_shape(int32_t model, int32_t n, int32_t &m, int32_t &d, int32_t &units) {
+    switch (model) {
+    case SDEB_KURAMOTO: m = n; d = n + 2; units = n; return true;
+    case SDEB_KURAMOTO_PAPER: m = n; d = 2 * n + 1; units = n; return true;
+    case SDEB_FHN_NET:
+        if (n % 2) return false;
+        m = n / 2; d = 6; units = n / 2; return true;
+    case SDEB_OU:
+    case SDEB_GBM: m = n; d = 2; units = n; return true;
+    case SDEB_LINEAR_ODE: m = 0; d = 1; units = n; return true;
+    default: return false;
+    }
+}
+
+bool mul_ok(int64_t a, int64_t b, int64_t &out) {
+    if (a < 0 || b < 0) return false;
+    if (a != 0 && b > INT64_MAX / a) return false;
+    out = a * b;
+    return true;
+}
+
+void free_buffers(sdeb_ctx *c) {
+    cudaFree(c->d_params);
+    cudaFree(c->d_x);
+    cudaFree(c->d_comp);
+    cudaFree(c->d_frames);
+    cudaFree(c->d_ckpt);
+    cudaFree(c->d_ckpt_comp);
+    cudaFree(c->d_flags);
+    c->d_params = c->d_x = c->d_frames = c->d_ckpt = nullptr;
+    c->d_comp = c->d_ckpt_comp = nullptr;
+    c->d_flags = nullptr;
+}
+
+sdeb_status validate(const sdeb_problem *pb, int32_t &units) {
+    if (!pb) return fail(nullptr, SDEB_EINVAL, "problem is NULL");
+    int32_t m = 0, d = 0;
+    if (pb->n <= 0) return fail(nullptr, SDEB_EINVAL, "n must be positive (got %d)", pb->n);
+    if (!model_shape(pb->model, pb->n, m, d, units))
+        return fail(nullptr, SDEB_EINVAL, "unknown model %d or n=%d invalid for it", pb->model, pb->n);
+    if (pb->m != m || pb->d != d)
+        return fail(nullptr, SDEB_EINVAL, "model %d with n=%d needs m=%d d=%d (got m=%d d=%d)", pb->model,
+                    pb->n, m, d, pb->m, pb->d);
+    if (pb->orbits <= 0) return fail(nullptr, SDEB_EINVAL, "orbits must be positive");
+    if (!(pb->dt > 0.0) || !std::isfinite(pb->dt)) return fail(nullptr, SDEB_EINVAL, "dt must be positive and finite");
+    if (!std::isfinite(pb->t0)) return fail(nullptr, SDEB_EINVAL, "t0 must be finite");
+    if (pb->steps < 0 || pb->steps > 0xffffffffLL)
+        return fail(nullptr, SDEB_EINVAL, "steps must be in [0, 2^32)");
+    if (pb->stride < 1 || pb->stride > 0xffffffffLL)
+        return fail(nullptr, SDEB_EINVAL, "stride must be in [1, 2^32)");
+    if (pb->precision != SDEB_FP32_KAHAN && pb->precision != SDEB_FP64)
+        return fail(nullptr, SDEB_EINVAL, "unknown precision %d", pb->precision);
+    if (pb->ckpt_every < 0) return fail(nullptr, SDEB_EINVAL, "ckpt_every must be >= 0");
+    if (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES))
+        return fail(nullptr, SDEB_EINVAL, "unknown flag bits 0x%x", pb->flags);
+    if (pb->reserved != 0) return fail(nullptr, SDEB_EINVAL, "reserved field must be 0");
+    if (pb->orbit_offset < 0 || pb->orbit_offset + pb->orbits > 0x100000000LL)
+        return fail(nullptr, SDEB_EINVAL, "orbit_offset + orbits must not exceed 2^32");
+    Layout l;
+    if (!default_layout(units, l))
+        return fail(nullptr, SDEB_EUNSUPPORTED, "more than 256 units per orbit is not supported");
+    return SDEB_OK;
+}
+
+cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream_t s) {
+    const bool phase = a.model == kKuramoto || a.model == kKuramotoPaper;
+    if (phase) return fp64 ? launch_forward_kuramoto_f64(a, l, s) : launch_forward_kuramoto_f32(a, l, s);
+    return fp64 ? launch_forward_other_f64(a, l, s) : launch_forward_other_f32(a, l, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sdeb_status_string(sdeb_status s) {
+    switch (s) {
+    case SDEB_OK: return "ok";
+    case SDEB_EINVAL: return "invalid argument";
+    case SDEB_ENOMEM: return "out of memory";
+    case SDEB_ECUDA: return "CUDA error";
+    case SDEB_ETIMEOUT: return "device wait timed out";
+    case SDEB_ESTATE: return "call order violated";
+    case SDEB_EUNSUPPORTED: return "unsupported";
+    case SDEB_ENONFINITE: return "non-finite state";
+    default: return "unknown status";
+    }
+}
+
+const char *sdeb_last_error(const sdeb_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+sdeb_status sdeb_create(const sdeb_problem *pb, sdeb_ctx **out) {
+    if (!out) return fail(nullptr, SDEB_EINVAL, "out is NULL");
+    *out = nullptr;
+    int32_t units = 0;
+    sdeb_status st = validate(pb, units);
+    if (st != SDEB_OK) return st;
+
+    const size_t elem = pb->precision == SDEB_FP64 ? 8 : 4;
+    const bool shared = pb->flags & SDEB_FLAG_SHARED_PARAMS;
+    int64_t state_elems, param_elems, frame_elems = 0, ckpt_elems = 0;
+    int64_t nframes = (pb->flags & SDEB_FLAG_NO_FRAMES) ? 0 : pb->steps / pb->stride + 1;
+    int64_t nckpt = pb->ckpt_every > 0 ? (pb->steps + pb->ckpt_every - 1) / pb->ckpt_every + 1 : 0;
+    if (!mul_ok(pb->orbits, pb->n, state_elems) || !mul_ok(shared ? 1 : pb->orbits, pb->d, param_elems) ||
+        !mul_ok(nframes, state_elems, frame_elems) || !mul_ok(nckpt, state_elems, ckpt_elems) ||
+        frame_elems > INT64_MAX / 8 || ckpt_elems > INT64_MAX / 8)
+        return fail(nullptr, SDEB_EINVAL, "problem size overflows");
+
+    sdeb_ctx *c = new (std::nothrow) sdeb_ctx;
+    if (!c) return fail(nullptr, SDEB_ENOMEM, "host allocation failed");
+    c->pb = *pb;
+    c->units = units;
+    c->elem = elem;
+    c->nframes = nframes;
+    c->nckpt = nckpt;
+    default_layout(units, c->layout);
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+    c->params_bytes = (size_t)param_elems * elem;
+    struct {
+        void **p;
+        size_t bytes;
+        const char *what;
+    } allocs[] = {
+        {&c->d_params, c->params_bytes, "parameters"},
+        {&c->d_x, (size_t)state_elems * elem, "state"},
+        {(void **)&c->d_comp, elem == 4 ? (size_t)state_elems * 4 : 0, "compensation"},
+        {&c->d_frames, (size_t)frame_elems * elem, "frames"},
+        {&c->d_ckpt, (size_t)ckpt_elems * elem, "checkpoints"},
+        {(void **)&c->d_ckpt_comp, elem == 4 ? (size_t)ckpt_elems * 4 : 0, "checkpoint compensation"},
+        {(void **)&c->d_flags, (size_t)pb->orbits, "flags"},
+    };
+    for (auto &a : allocs) {
+        if (a.bytes == 0) continue;
+        e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            sdeb_status s = cuda_fail(nullptr, e, a.what);
+            free_buffers(c);
+            delete c;
+            return s;
+        }
+    }
+    *out = c;
+    return SDEB_OK;
+}
+
+void sdeb_destroy(sdeb_ctx *ctx) {
+    if (!ctx) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    free_buffers(ctx);
+    cudaSetDevice(prev);
+    delete ctx;
+}
+
+sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0, int32_t on_device,
+                            void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (!params || !x0) return fail(ctx, SDEB_EINVAL, "params and x0 must not be NULL");
+    const cudaStream_t s = as_stream(stream);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t state_bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
+    cudaError_t e = cudaMemcpyAsync(ctx->d_params, params, ctx->params_bytes, kind, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_x, x0, state_bytes, kind, s);
+    if (e == cudaSuccess && ctx->d_comp) e = cudaMemsetAsync(ctx->d_comp, 0, state_bytes, s);
+    if (e == cudaSuccess && ctx->d_frames)
+        e = cudaMemcpyAsync(ctx->d_frames, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && ctx->d_ckpt)
+        e = cudaMemcpyAsync(ctx->d_ckpt, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && ctx->d_ckpt_comp) e = cudaMemsetAsync(ctx->d_ckpt_comp, 0, state_bytes, s);
+    if (e == cudaSuccess && ctx->d_flags) e = cudaMemsetAsync(ctx->d_flags, 0, (size_t)ctx->pb.orbits, s);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->params_set = false;
+        return cuda_fail(ctx, e, "sdeb_set_params copy");
+    }
+    ctx->params_set = true;
+    ctx->k_current = 0;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
+    if (k_begin != ctx->k_current)
+        return fail(ctx, SDEB_ESTATE, "k_begin=%lld but the state is at step %lld", (long long)k_begin,
+                    (long long)ctx->k_current);
+    if (k_end < k_begin || k_end > ctx->pb.steps)
+        return fail(ctx, SDEB_EINVAL, "k_end=%lld outside [k_begin, steps]", (long long)k_end);
+    if (k_end == k_begin) return SDEB_OK;
+    ForwardArgs a{};
+    a.model = ctx->pb.model;
+    a.n = ctx->pb.n;
+    a.units = ctx->units;
+    a.orbits = ctx->pb.orbits;
+    a.params = ctx->d_params;
+    a.param_stride = (ctx->pb.flags & SDEB_FLAG_SHARED_PARAMS) ? 0 : ctx->pb.d;
+    a.x = ctx->d_x;
+    a.comp = ctx->d_comp;
+    a.frames = ctx->d_frames;
+    a.nframes = ctx->nframes;
+    a.ckpt = ctx->d_ckpt;
+    a.ckpt_comp = ctx->d_ckpt_comp;
+    a.ckpt_every = (uint32_t)ctx->pb.ckpt_every;
+    a.k_begin = (uint32_t)k_begin;
+    a.k_end = (uint32_t)k_end;
+    a.stride = (uint32_t)ctx->pb.stride;
+    a.orbit_offset = (uint32_t)ctx->pb.orbit_offset;
+    a.dt = ctx->pb.dt;
+    a.flags = ctx->d_flags;
+    a.keys = philox_key_schedule(ctx->pb.seed);
+    cudaError_t e = launch_forward(a, ctx->layout, ctx->pb.precision == SDEB_FP64, as_stream(stream));
+    if (e == cudaErrorNotSupported)
+        return fail(ctx, SDEB_EUNSUPPORTED, "no kernel for model %d with layout G=%d P=%d", a.model,
+                    ctx->layout.G, ctx->layout.P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "forward kernel launch");
+    ctx->k_current = k_end;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_integrate(sdeb_ctx *ctx, void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->params_set && ctx->k_current != 0)
+        return fail(ctx, SDEB_ESTATE, "state is at step %lld; call sdeb_set_params to restart",
+                    (long long)ctx->k_current);
+    return sdeb_integrate_range(ctx, 0, ctx->pb.steps, stream);
+}
+
+sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int64_t frame_begin,
+                             int64_t frame_count, int32_t dst_on_device, void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
+    if (!ctx->d_frames) return fail(ctx, SDEB_ESTATE, "context was created without frames");
+    if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
+    if (frame_begin < 0 || frame_count < 0 || frame_begin + frame_count > ctx->nframes)
+        return fail(ctx, SDEB_EINVAL, "frames [%lld, %lld) outside [0, %lld)", (long long)frame_begin,
+                    (long long)(frame_begin + frame_count), (long long)ctx->nframes);
+    if (frame_count > 0 && (frame_begin + frame_count - 1) * ctx->pb.stride > ctx->k_current)
+        return fail(ctx, SDEB_ESTATE, "frame %lld is past the current step %lld",
+                    (long long)(frame_begin + frame_count - 1), (long long)ctx->k_current);
+    const size_t frame_bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
+    if (dst_bytes != frame_bytes * (size_t)frame_count)
+        return fail(ctx, SDEB_EINVAL, "dst_bytes=%zu, expected %zu", dst_bytes, frame_bytes * (size_t)frame_count);
+    if (frame_count == 0) return SDEB_OK;
+    const cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(dst, static_cast<char *>(ctx->d_frames) + frame_bytes * frame_begin,
+                                    dst_bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sdeb_read_orbits copy");
+    }
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t dst_on_device, void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
+    if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
+    const size_t bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
+    if (dst_bytes != bytes) return fail(ctx, SDEB_EINVAL, "dst_bytes=%zu, expected %zu", dst_bytes, bytes);
+    const cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(dst, ctx->d_x, bytes,
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sdeb_read_final copy");
+    }
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
+    if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
+    const cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(dst, ctx->d_flags, (size_t)ctx->pb.orbits, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sdeb_orbit_flags copy");
+    }
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *bytes) {
+    if (!ctx || !ptr || !bytes) return fail(ctx, SDEB_EINVAL, "NULL argument");
+    *ptr = ctx->d_frames;
+    *bytes = ctx->d_frames ? (size_t)ctx->nframes * ctx->pb.orbits * ctx->pb.n * ctx->elem : 0;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_dx0, void *stream) {
+    (void)dL_dxK; (void)dL_dp; (void)dL_dx0; (void)stream;
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    return fail(ctx, SDEB_EUNSUPPORTED, "adjoint not available");
+}
+
+sdeb_status sdeb_philox_fill(uint64_t seed, uint32_t k0, int64_t nk, uint32_t b0, int64_t nb, uint32_t o0,
+                             int64_t no, uint32_t stream_id, uint32_t *out, void *stream) {
+    if (nk < 0 || nb < 0 || no < 0) return fail(nullptr, SDEB_EINVAL, "negative extent");
+    if (nk > 0x100000000LL || nb > 0x100000000LL || no > 0x100000000LL)
+        return fail(nullptr, SDEB_EINVAL, "extent beyond the 32-bit counter range");
+    int64_t t;
+    if (!mul_ok(nk, nb, t) || !mul_ok(t, no, t) || t > INT64_MAX / 16)
+        return fail(nullptr, SDEB_EINVAL, "size overflows");
+    if (t > 0 && !out) return fail(nullptr, SDEB_EINVAL, "out is NULL");
+    cudaError_t e = launch_philox_fill(seed, k0, nk, b0, nb, o0, no, stream_id, out, as_stream(stream));
+    return e == cudaSuccess ? SDEB_OK : cuda_fail(nullptr, e, "philox_fill launch");
+}
+
+sdeb_status sdeb_normals_fill(uint64_t seed, uint32_t k0, int64_t nk, uint32_t o0, int64_t no, int32_t m,
+                              int32_t precision, void *out, void *stream) {
+    if (nk < 0 || no < 0 || m < 0) return fail(nullptr, SDEB_EINVAL, "negative extent");
+    if (nk > 0x100000000LL || no > 0x100000000LL)
+        return fail(nullptr, SDEB_EINVAL, "extent beyond the 32-bit counter range");
+    if (precision != SDEB_FP32_KAHAN && precision != SDEB_FP64)
+        return fail(nullptr, SDEB_EINVAL, "unknown precision %d", precision);
+    int64_t t;
+    if (!mul_ok(nk, no, t) || !mul_ok(t, m, t) || t > INT64_MAX / 8)
+        return fail(nullptr, SDEB_EINVAL, "size overflows");
+    if (t > 0 && !out) return fail(nullptr, SDEB_EINVAL, "out is NULL");
+    cudaError_t e = launch_normals_fill(seed, k0, nk, o0, no, m, precision == SDEB_FP64, out, as_stream(stream));
+    return e == cudaSuccess ? SDEB_OK : cuda_fail(nullptr, e, "normals_fill launch");
+}
+
+sdeb_status sdeb_order_param(const void *theta, int64_t orbits, int32_t n, int32_t precision, void *r,
+                             void *dr, void *stream) {
+    if (orbits < 0 || n <= 0) return fail(nullptr, SDEB_EINVAL, "orbits >= 0 and n > 0 required");
+    if (precision != SDEB_FP32_KAHAN && precision != SDEB_FP64)
+        return fail(nullptr, SDEB_EINVAL, "unknown precision %d", precision);
+    if (orbits > 0 && (!theta || !r)) return fail(nullptr, SDEB_EINVAL, "theta and r must not be NULL");
+    cudaError_t e = launch_order_param(theta, orbits, n, precision == SDEB_FP64, r, dr, as_stream(stream));
+    return e == cudaSuccess ? SDEB_OK : cuda_fail(nullptr, e, "order_param launch");
+}
+
+}  // extern "C"
