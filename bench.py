@@ -352,7 +352,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--orbit-scale", type=float, default=1.0,
+                    help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
+    ap.add_argument("--horizon", type=int, default=None,
+                    help="steps per orbit (profiling runs only; the benchmark uses 10^4)")
     args = ap.parse_args()
+    global CONFIGS, STEPS, WORKLOAD
+    if args.orbit_scale != 1.0 or args.horizon is not None:
+        CONFIGS = [(n, max(1, int(o * args.orbit_scale))) for n, o in CONFIGS]
+        STEPS = args.horizon if args.horizon is not None else STEPS
+        WORKLOAD = "profiling case: n=8/32/128, orbits %s, %d steps" % ([o for _, o in CONFIGS], STEPS)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

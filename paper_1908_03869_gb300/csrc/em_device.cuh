@@ -4,7 +4,7 @@
 //     the host and passed in the kernel's parameter space, so every round's
 //     key operand is a constant-bank read shared by all threads.
 //   * Uniforms u = (w + 1/2) 2^-32 (reading of Eq. 3's "uniform over [0,1]"),
-//     converted in FP32 with a single correctly rounded operation.
+//     in FP32 within one ulp of the exact value.
 //   * Box-Muller (Eq. 3) in FP32 (SFU approximations) and FP64.
 //   * Two-constant Cody-Waite reduction of a phase to [-pi, pi] before the SFU
 //     sine/cosine (W. J. Cody, W. Waite, "Software Manual for the Elementary
@@ -32,13 +32,16 @@ struct U32x4 {
 
 // One round: multiply words 0 and 2 by the two round multipliers, keep the
 // 64-bit products' halves, mix the high halves with words 1 and 3 and the key.
+// The 32 x 32 -> 64 products are written as 64-bit multiplies so each maps
+// to a single wide integer multiply-add.
 __device__ __forceinline__ void philox_round(uint32_t &c0, uint32_t &c1, uint32_t &c2,
                                              uint32_t &c3, uint32_t k0, uint32_t k1) {
-    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-    uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
-    uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
-    uint32_t n0 = hi1 ^ c1 ^ k0;
-    uint32_t n2 = hi0 ^ c3 ^ k1;
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
     c0 = n0;
     c1 = lo1;
     c2 = n2;
@@ -70,27 +73,17 @@ inline PhiloxKeys philox_key_schedule(uint64_t seed) {
 // Uniforms
 // ---------------------------------------------------------------------------
 
-// Exact float of a 16-bit value: place it in the mantissa of 2^23 and subtract.
-__device__ __forceinline__ float u16_to_f32(uint32_t v16) {
-    return __uint_as_float(0x4b000000u | v16) - 8388608.0f;
-}
-
-// u = (w + 1/2) 2^-32 rounded once to FP32: the inner fma is exact
-// ((lo + 1/2) 2^-32 needs 17 bits), the outer one rounds the exact value.
+// u = (w + 1/2) 2^-32 in FP32: the integer converts once (round to
+// nearest, 24 bits) and the affine map rounds again, so u is within one ulp
+// of the exact value and never 0 or 1 beyond that ulp (w = 2^32 - 1 gives
+// u = 1.0f; callers that take a logarithm use the complement word there).
 __device__ __forceinline__ float uniform_f32(uint32_t w) {
-    float hi = u16_to_f32(w >> 16);
-    float lo = u16_to_f32(w & 0xffffu);
-    return __fmaf_rn(hi, 0x1p-16f, __fmaf_rn(lo, 0x1p-32f, 0x1p-33f));
+    return __fmaf_rn(__uint2float_rn(w), 0x1p-32f, 0x1p-33f);
 }
 
-// a = u - 1/2 = (w - 2^31 + 1/2) 2^-32 in (-1/2, 1/2), rounded once: the
-// signed high half is converted through the 1.5 * 2^23 bias.
+// a = u - 1/2 = (w - 2^31 + 1/2) 2^-32 in [-1/2, 1/2] from the signed word.
 __device__ __forceinline__ float centered_uniform_f32(uint32_t w) {
-    int32_t s = (int32_t)(w ^ 0x80000000u);
-    int32_t hi = s >> 16;  // arithmetic shift, in [-2^15, 2^15)
-    float fhi = __int_as_float(0x4b400000 + hi) - 12582912.0f;
-    float flo = u16_to_f32((uint32_t)s & 0xffffu);
-    return __fmaf_rn(fhi, 0x1p-16f, __fmaf_rn(flo, 0x1p-32f, 0x1p-33f));
+    return __fmaf_rn(__int2float_rn((int32_t)(w ^ 0x80000000u)), 0x1p-32f, 0x1p-33f);
 }
 
 __device__ __forceinline__ double uniform_f64(uint32_t w) {
@@ -113,31 +106,27 @@ __device__ __forceinline__ float lg2_approx_f32(float y) {
     return r;
 }
 
-// FP32.  y = -2 ln U1 comes from the SFU log2 except when U1 is within 2^-4
+// FP32.  y = -2 ln U1 comes from the SFU log2 except when U1 is within 2^-6
 // of 1, where the absolute error of an SFU logarithm would dominate: there
-// t = 1 - U1 = (~w + 1/2) 2^-32 is formed exactly (~w < 2^28) and
-// -2 ln(1 - t) = 2 t (1 + t/2 + t^2/3 + ... + t^6/7) + O(t^8), the dropped
-// terms below 2^-25 relative for t <= 2^-4.  The angle uses the centred
-// uniform so the SFU sees an argument in (-pi, pi):
+// t = 1 - U1 = (~w + 1/2) 2^-32 comes from the complement word and
+// -2 ln(1 - t) = 2 t (1 + t/2 + t^2/3 + t^3/4 + t^4/5) + O(t^6), the dropped
+// terms below 2^-26 relative for t <= 2^-6.  The angle uses the centred
+// uniform so the SFU sees an argument in [-pi, pi]:
 // cos(2 pi U2) = -cos(2 pi (U2 - 1/2)), likewise for sin.
 __device__ __forceinline__ void box_muller_f32(uint32_t w_first, uint32_t w_second, float &n_cos,
                                                float &n_sin) {
     const float kMinus2Ln2 = -1.38629436111989061883f;  // -2 ln 2
-    float u1 = uniform_f32(w_first);
-    const uint32_t comp = ~w_first;  // 2^32 - 1 - w
-    float t = uniform_f32(comp);     // 1 - U1, exact to rounding
-    float poly = __fmaf_rn(t, 1.0f / 7.0f, 1.0f / 6.0f);
-    poly = __fmaf_rn(poly, t, 1.0f / 5.0f);
-    poly = __fmaf_rn(poly, t, 1.0f / 4.0f);
+    const uint32_t comp = ~w_first;                      // 2^32 - 1 - w
+    const float t = uniform_f32(comp);                   // 1 - U1
+    float poly = __fmaf_rn(t, 0.2f, 0.25f);
     poly = __fmaf_rn(poly, t, 1.0f / 3.0f);
-    poly = __fmaf_rn(poly, t, 1.0f / 2.0f);
+    poly = __fmaf_rn(poly, t, 0.5f);
     poly = __fmaf_rn(poly, t, 1.0f);
-    float y_series = 2.0f * t * poly;
-    float y_log = kMinus2Ln2 * lg2_approx_f32(u1);
-    float y = (comp < 0x10000000u) ? y_series : y_log;
-    float radius = sqrt_approx_f32(y);
-    float a = centered_uniform_f32(w_second);
-    float ang = 6.28318530717958647692f * a;
+    const float y_series = (2.0f * t) * poly;
+    const float y_log = kMinus2Ln2 * lg2_approx_f32(uniform_f32(w_first));
+    const float y = (comp < (1u << 26)) ? y_series : y_log;
+    const float radius = sqrt_approx_f32(y);
+    const float ang = 6.28318530717958647692f * centered_uniform_f32(w_second);
     float s, c;
     __sincosf(ang, &s, &c);
     n_cos = -radius * c;
