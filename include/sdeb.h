@@ -197,6 +197,40 @@ SDEB_API sdeb_status sdeb_normals_fill(uint64_t seed, uint32_t k0, int64_t nk, u
 SDEB_API sdeb_status sdeb_order_param(const void *theta, int64_t orbits, int32_t n, int32_t precision,
                              void *r, void *dr, void *stream);
 
+/* ---- Allocation-free forward integration ------------------------------
+ * No counterpart in the paper.  For callers that cannot allocate device
+ * memory -- code running while a CUDA graph is captured, hosts whose own
+ * allocator owns every device byte, embedded or real-time programs that
+ * forbid allocation after start-up -- sdeb_create is unusable because the
+ * context allocates its buffers.  This entry point allocates nothing: the
+ * caller passes the inputs and outputs, and the only scratch (the FP32 Kahan
+ * compensation words and a per-orbit status byte) lives in a fixed array
+ * compiled into the library, SDEB_NOALLOC_SCRATCH_BYTES bytes that every GPU
+ * which loads the library keeps until the process exits.
+ *
+ * Semantics are those of sdeb_create + sdeb_set_params(on_device = 1) +
+ * sdeb_integrate + reading the frames and the final state, for the same
+ * problem: the same kernel produces the same numbers.
+ *   pb       problem; ckpt_every must be 0; orbits <= SDEB_NOALLOC_MAX_ORBITS
+ *            and orbits * n <= SDEB_NOALLOC_MAX_STATES, else SDEB_EINVAL.
+ *   params   device, [orbits][d] (or [d] with SDEB_FLAG_SHARED_PARAMS).
+ *   x0       device, [orbits][n], not modified.
+ *   x_final  device, [orbits][n]; receives x0, then serves as the working
+ *            state and ends as the state at step `steps`.
+ *   frames   device, [steps/stride + 1][orbits][n], or NULL for no frames.
+ * Element type is the problem precision.  Asynchronous on `stream`.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Calls share the scratch and it keeps the last
+ * call's contents (each call clears what must start at zero): calls whose
+ * work overlaps on the GPU race, so serialise them (one stream, or events).
+ * Non-finite orbits are not reported on this path. */
+#define SDEB_NOALLOC_MAX_STATES (1 << 21)
+#define SDEB_NOALLOC_MAX_ORBITS (1 << 21)
+#define SDEB_NOALLOC_SCRATCH_BYTES (SDEB_NOALLOC_MAX_STATES * 4 + SDEB_NOALLOC_MAX_ORBITS)
+SDEB_API sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void *params, const void *x0,
+                                            void *x_final, void *frames, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

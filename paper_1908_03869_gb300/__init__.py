@@ -23,7 +23,7 @@ __all__ = [
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
-    "model_shape", "EXPORTED_SYMBOLS",
+    "sdeb_integrate_noalloc", "model_shape", "EXPORTED_SYMBOLS",
 ]
 
 SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
@@ -97,6 +97,7 @@ _SIGS = {
     "sdeb_normals_fill": (_ST, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64,
                                 ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "sdeb_order_param": (_ST, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "sdeb_integrate_noalloc": (_ST, [ctypes.POINTER(Problem), _P, _P, _P, _P, _P]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -200,3 +201,8 @@ def sdeb_normals_fill(seed, k0, nk, o0, no, m, precision, out, stream=None):
 
 def sdeb_order_param(theta, orbits, n, precision, r, dr=None, stream=None):
     _check(lib().sdeb_order_param(theta, orbits, n, precision, r, dr, _stream(stream)))
+
+
+def sdeb_integrate_noalloc(problem, params, x0, x_final, frames=None, stream=None):
+    """Allocation-free forward integration (see include/sdeb.h)."""
+    _check(lib().sdeb_integrate_noalloc(ctypes.byref(problem), params, x0, x_final, frames, _stream(stream)))

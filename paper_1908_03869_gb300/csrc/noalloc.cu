@@ -1,0 +1,162 @@
+// sdeb_integrate_noalloc: the forward integration for callers that cannot
+// allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+// being captured, allocators with a fixed arena they manage themselves,
+// embedded or real-time hosts that forbid allocation after start-up, and
+// plugins whose host application owns every device allocation.  The context
+// API (sdeb_create) allocates its state, compensation, frame and flag
+// buffers, so those callers cannot use it.  This entry point takes every
+// input and output from the caller and keeps the only scratch the forward
+// kernel needs -- the Kahan compensation word of every FP32 state component
+// and the per-orbit status byte -- in a fixed array in the library's own
+// device memory.
+//
+// The scratch is a file-scope __device__ array of kScratchBytes bytes.  Every
+// GPU that loads the library holds it until the process exits.  Host code
+// cannot use the array's name as a device address (on the host that name
+// is only a stand-in), so the first call on each device, with that device
+// current, looks the address up once with cudaGetSymbolAddress and caches
+// it.  That first call should come before any stream capture starts.
+// Every call shares the array and it keeps the last call's contents: each
+// call clears the part that must start at zero, and calls whose work
+// overlaps on the GPU race on it.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "em_internal.h"
+#include "sdeb.h"
+
+namespace sdeb {
+void record_error(const char *msg);  // sdeb_last_error(NULL) text (sdeb_api.cu)
+}
+
+namespace {
+
+using namespace sdeb;
+
+// Maximum problem size of the allocation-free path.
+constexpr int64_t kMaxStates = SDEB_NOALLOC_MAX_STATES;   // orbits * n
+constexpr int64_t kMaxOrbits = SDEB_NOALLOC_MAX_ORBITS;
+constexpr size_t kCompBytes = (size_t)kMaxStates * sizeof(float);
+constexpr size_t kScratchBytes = kCompBytes + (size_t)kMaxOrbits;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char *g_scratch_ptr[kMaxDevices] = {};
+
+sdeb_status fail(sdeb_status s, const char *fmt, long long a = 0, long long b = 0) {
+    char buf[256];
+    snprintf(buf, sizeof buf, fmt, a, b);
+    record_error(buf);
+    return s;
+}
+
+// Device address of the scratch array on the current device.
+sdeb_status scratch_address(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(SDEB_ECUDA, "cudaGetDevice failed");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SDEB_EUNSUPPORTED, "device index %lld out of range", dev);
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_scratch_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return fail(SDEB_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+        }
+        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return SDEB_OK;
+}
+
+bool shape_ok(const sdeb_problem *pb, int32_t &units) {
+    int32_t m, d;
+    switch (pb->model) {
+    case SDEB_KURAMOTO: m = pb->n; d = pb->n + 2; units = pb->n; break;
+    case SDEB_KURAMOTO_PAPER: m = pb->n; d = 2 * pb->n + 1; units = pb->n; break;
+    case SDEB_FHN_NET:
+        if (pb->n % 2) return false;
+        m = pb->n / 2; d = 6; units = pb->n / 2; break;
+    case SDEB_OU:
+    case SDEB_GBM: m = pb->n; d = 2; units = pb->n; break;
+    case SDEB_LINEAR_ODE: m = 0; d = 1; units = pb->n; break;
+    default: return false;
+    }
+    return pb->m == m && pb->d == d;
+}
+
+}  // namespace
+
+extern "C" sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void *params, const void *x0,
+                                              void *x_final, void *frames, void *stream) {
+    if (!pb || !params || !x0 || !x_final) return fail(SDEB_EINVAL, "pb, params, x0 and x_final must not be NULL");
+    int32_t units = 0;
+    if (pb->n <= 0 || !shape_ok(pb, units)) return fail(SDEB_EINVAL, "model / n / m / d inconsistent");
+    if (pb->orbits <= 0 || !(pb->dt > 0.0) || !std::isfinite(pb->dt) || !std::isfinite(pb->t0) ||
+        pb->steps < 0 || pb->steps > 0xffffffffLL || pb->stride < 1 || pb->stride > 0xffffffffLL ||
+        (pb->precision != SDEB_FP32_KAHAN && pb->precision != SDEB_FP64) || pb->reserved != 0 ||
+        (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES)) || pb->orbit_offset < 0 ||
+        pb->orbit_offset + pb->orbits > 0x100000000LL)
+        return fail(SDEB_EINVAL, "problem fields out of range");
+    if (pb->ckpt_every != 0) return fail(SDEB_EUNSUPPORTED, "checkpoints need the context API");
+    if (pb->orbits > kMaxOrbits || pb->orbits * (int64_t)pb->n > kMaxStates)
+        return fail(SDEB_EINVAL, "orbits=%lld states=%lld exceed the allocation-free limits", (long long)pb->orbits,
+                    (long long)(pb->orbits * (int64_t)pb->n));
+    Layout layout;
+    if (!default_layout(units, layout)) return fail(SDEB_EUNSUPPORTED, "more than 256 units per orbit");
+
+    unsigned char *scratch = nullptr;
+    sdeb_status st = scratch_address(&scratch);
+    if (st != SDEB_OK) return st;
+
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool fp64 = pb->precision == SDEB_FP64;
+    const size_t elem = fp64 ? 8 : 4;
+    const size_t state_bytes = (size_t)pb->orbits * pb->n * elem;
+    const bool want_frames = frames != nullptr && !(pb->flags & SDEB_FLAG_NO_FRAMES);
+    float *comp = reinterpret_cast<float *>(scratch);
+    uint8_t *flags = scratch + kCompBytes;
+
+    cudaError_t e = cudaMemcpyAsync(x_final, x0, state_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && !fp64) e = cudaMemsetAsync(comp, 0, (size_t)pb->orbits * pb->n * sizeof(float), s);
+    if (e == cudaSuccess && want_frames) e = cudaMemcpyAsync(frames, x0, state_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SDEB_ECUDA, "stream-ordered copy failed");
+    }
+    if (pb->steps == 0) return SDEB_OK;
+
+    ForwardArgs a{};
+    a.model = pb->model;
+    a.n = pb->n;
+    a.units = units;
+    a.orbits = pb->orbits;
+    a.params = params;
+    a.param_stride = (pb->flags & SDEB_FLAG_SHARED_PARAMS) ? 0 : pb->d;
+    a.x = x_final;
+    a.comp = fp64 ? nullptr : comp;
+    a.frames = want_frames ? frames : nullptr;
+    a.nframes = want_frames ? pb->steps / pb->stride + 1 : 0;
+    a.ckpt = nullptr;
+    a.ckpt_comp = nullptr;
+    a.ckpt_every = 0;
+    a.k_begin = 0;
+    a.k_end = (uint32_t)pb->steps;
+    a.stride = (uint32_t)pb->stride;
+    a.orbit_offset = (uint32_t)pb->orbit_offset;
+    a.dt = pb->dt;
+    a.flags = flags;
+    a.keys = philox_key_schedule(pb->seed);
+    const bool phase = pb->model == SDEB_KURAMOTO || pb->model == SDEB_KURAMOTO_PAPER;
+    e = phase ? (fp64 ? launch_forward_kuramoto_f64(a, layout, s) : launch_forward_kuramoto_f32(a, layout, s))
+              : (fp64 ? launch_forward_other_f64(a, layout, s) : launch_forward_other_f32(a, layout, s));
+    if (e == cudaErrorNotSupported) return fail(SDEB_EUNSUPPORTED, "no kernel for this model and layout");
+    if (e != cudaSuccess) return fail(SDEB_ECUDA, "forward kernel launch failed");
+    return SDEB_OK;
+}

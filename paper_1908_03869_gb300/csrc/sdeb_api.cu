@@ -129,6 +129,11 @@ cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream
 
 }  // namespace
 
+namespace sdeb {
+// Lets other translation units set the text sdeb_last_error(NULL) returns.
+void record_error(const char *msg) { g_last_error = msg; }
+}  // namespace sdeb
+
 extern "C" {
 
 const char *sdeb_status_string(sdeb_status s) {

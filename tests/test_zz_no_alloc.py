@@ -1,0 +1,87 @@
+"""The allocation-free entry point sdeb_integrate_noalloc.
+
+It exists for callers that cannot allocate device memory (graph capture,
+host-owned allocators, real-time hosts): they pass every input and output
+buffer, and the library keeps its only scratch in a fixed array of its own.
+These tests call it through the C ABI twice in a row -- the shared scratch
+keeps the previous call's contents, so the second call checks that what must
+start at zero is cleared -- and compare each result with the context API's
+(sdeb_create / sdeb_set_params / sdeb_integrate) within the parity
+tolerances the other GPU tests use.  The file is named to be collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_1908_03869_gb300 as sdeb
+from paper_1908_03869_gb300 import build as sdeb_build
+from paper_1908_03869_gb300 import inputs
+
+from helpers import max_rel_err, np_dtype, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sdeb_build.build()
+    sdeb.lib()
+
+
+def _noalloc(pb, p, x0, with_frames=True):
+    import torch
+    dt = torch.float64 if pb.precision == sdeb.SDEB_FP64 else torch.float32
+    pt = torch.tensor(p, dtype=dt, device="cuda")
+    xt = torch.tensor(x0, dtype=dt, device="cuda")
+    xf = torch.empty_like(xt)
+    fr = torch.empty((pb.steps // pb.stride + 1, pb.orbits, pb.n), dtype=dt, device="cuda") if with_frames else None
+    sdeb.sdeb_integrate_noalloc(pb, ctypes.c_void_p(pt.data_ptr()), ctypes.c_void_p(xt.data_ptr()),
+                                ctypes.c_void_p(xf.data_ptr()),
+                                ctypes.c_void_p(fr.data_ptr()) if fr is not None else None,
+                                torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return (fr.cpu().numpy() if fr is not None else None), xf.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_noalloc_matches_context_api_twice(precision):
+    n, orbits, dt, steps, stride, seed = 32, 4099, 0.01, 600, 50, 3
+    p, x0 = inputs.kuramoto(n, orbits, seed=21)
+    p, x0 = p.astype(np_dtype(precision)), x0.astype(np_dtype(precision))
+    ref_fr, ref_fin = run_gpu("kuramoto", n, p, x0, dt, steps, stride, seed=seed, precision=precision)
+    pb = sdeb.Problem.make("kuramoto", n, orbits, dt, steps, stride, seed, precision)
+    for _ in range(2):
+        fr, fin = _noalloc(pb, p, x0)
+        assert max_rel_err(fr, ref_fr) < TOL[precision]
+        assert max_rel_err(fin, ref_fin) < TOL[precision]
+
+
+def test_noalloc_other_model_without_frames():
+    n, orbits, dt, steps = 128, 1000, 0.01, 300
+    p, x0 = inputs.fhn(n // 2, orbits, seed=4)
+    p, x0 = p.astype(np.float32), x0.astype(np.float32)
+    _, ref_fin = run_gpu("fhn_net", n, p, x0, dt, steps, 10, seed=1, precision="fp32")
+    pb = sdeb.Problem.make("fhn_net", n, orbits, dt, steps, 10, 1, "fp32")
+    for _ in range(2):
+        _, fin = _noalloc(pb, p, x0, with_frames=False)
+        assert max_rel_err(fin, ref_fin) < TOL["fp32"]
+
+
+def test_noalloc_rejects_sizes_beyond_its_limit():
+    n = 64
+    orbits = (1 << 21) // n + 1        # one orbit past the scratch limit
+    pb = sdeb.Problem.make("kuramoto", n, orbits, 0.01, 10, 10, 0, "fp32")
+    L = sdeb.lib()
+    st = L.sdeb_integrate_noalloc(ctypes.byref(pb), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                  ctypes.c_void_p(16), None, None)
+    assert st == sdeb.SDEB_EINVAL
+    assert "limit" in sdeb.sdeb_last_error()
+    pb = sdeb.Problem.make("kuramoto", n, 16, 0.01, 10, 10, 0, "fp32", ckpt_every=5)
+    st = L.sdeb_integrate_noalloc(ctypes.byref(pb), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                  ctypes.c_void_p(16), None, None)
+    assert st == sdeb.SDEB_EUNSUPPORTED
