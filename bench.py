@@ -201,6 +201,14 @@ def run_ours(args):
         pt, xt = torch.tensor(p, dtype=dtype), torch.tensor(x0, dtype=dtype)
         dev_inputs.append((pt.cuda(), xt.cuda()))
         host_inputs.append((pt.pin_memory(), xt.pin_memory()))
+    # pick each problem's lane-group layout once, outside the timed region
+    layouts = {}
+    for i, it in enumerate(its):
+        it.set_params(*dev_inputs[i], stream=stream)
+        if not args.no_autotune:
+            it.autotune(trial_steps=64, stream=stream)
+        layouts[str(it.pb.n)] = list(it.layout())
+    torch.cuda.synchronize()
     units_per_step = sum(o * STEPS for _, o in CONFIGS)
     osc_per_step = sum(n * o * STEPS for n, o in CONFIGS)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # 512 MiB > 129 MB L2
@@ -309,6 +317,12 @@ def run_ours(args):
         fp64 = {"value": u64 / t64, "unit": "orbit-steps/s", "steps_per_orbit": steps64,
                 "note": "same orbits, first 1000 of the 10^4 steps; cost per step is constant over the horizon"}
 
+    # ---- forward + adjoint (n = 32, 16384 orbits sharing one parameter
+    # vector, 2000 steps, checkpoints every 100, loss = mean order parameter)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = _time_adjoint(stream, rank)
+
     # ---- CPU oracle on this host's cores --------------------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -329,18 +343,79 @@ def run_ours(args):
                        "l2": "flushed between steps (512 MiB write)", "parallelism": "orbits sharded, no collective"},
             "oscillator_steps_per_sec": value * osc_per_step / units_per_step,
             "wall_s": wall,
-            "per_launch_ms": per_launch_ms,
+            "per_launch_ms": per_launch_ms, "layouts_G_P": layouts,
             "roofline": {"bound": "alu", "pipe": "SFU (MUFU)", "achieved": achieved, "peak": peak,
                          "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
-            "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _time_adjoint(stream, rank, reps=5):
+    import ctypes
+
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    W = inputs.WORKLOADS["kuramoto_adjoint_n32"]
+    n, orbits = W["n"], W["orbits"]
+    p, x0 = inputs.kuramoto(n, orbits, seed=1, shared=True)
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    xt = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    mk = lambda ck: sdeb.Problem.make("kuramoto", n, orbits, W["dt"], W["steps"], 1, W["seed"], "fp32",
+                                      ckpt_every=ck, no_frames=True, shared_params=True,
+                                      orbit_offset=rank * orbits)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with Integrator(mk(0)) as plain, Integrator(mk(W["ckpt_every"])) as ck:
+        # dL/dX^K of the mean order parameter at T, from the library's kernel
+        for it in (plain, ck):
+            it.set_params(pt, xt, stream=stream)
+            it.autotune(trial_steps=64, stream=stream)
+        lay = plain.layout()
+        ck.set_layout(*lay)
+        ck.integrate(stream=stream)
+        xK = ck.final(stream=stream)
+        r = torch.empty(orbits, dtype=torch.float32, device="cuda")
+        dr = torch.empty_like(xK)
+        torch.cuda.synchronize()
+        sdeb.sdeb_order_param(ctypes.c_void_p(xK.data_ptr()), orbits, n, 0, ctypes.c_void_p(r.data_ptr()),
+                              ctypes.c_void_p(dr.data_ptr()), stream)
+        dL = (dr / orbits).contiguous()
+        torch.cuda.synchronize()
+        t_plain, t_fwd, t_adj = [], [], []
+        for _ in range(reps + 1):
+            a, b, c, d, e = ev(), ev(), ev(), ev(), ev()
+            plain.set_params(pt, xt, stream=stream)
+            a.record(stream)
+            plain.integrate(stream=stream)
+            b.record(stream)
+            ck.set_params(pt, xt, stream=stream)
+            c.record(stream)
+            ck.integrate(stream=stream)
+            d.record(stream)
+            ck.grad(dL, stream=stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            t_plain.append(a.elapsed_time(b))
+            t_fwd.append(c.elapsed_time(d))
+            t_adj.append(d.elapsed_time(e))
+    t_plain, t_fwd, t_adj = [statistics.median(t[1:]) for t in (t_plain, t_fwd, t_adj)]
+    units = orbits * W["steps"]
+    return {"workload": "kuramoto n=32, 16384 orbits, shared params, dt=0.01, 2000 steps, ckpt every 100, fp32",
+            "layout_G_P": list(lay),
+            "fwd_ms": t_plain, "fwd_ckpt_ms": t_fwd, "adjoint_ms": t_adj,
+            "fwd_plus_adjoint_orbit_steps_per_sec": units / ((t_fwd + t_adj) / 1e3),
+            "fwd_orbit_steps_per_sec": units / (t_plain / 1e3),
+            "ratio_fwd_plus_adjoint_to_fwd": (t_fwd + t_adj) / t_plain}
 
 
 def main():
@@ -352,6 +427,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--orbit-scale", type=float, default=1.0,
                     help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
     ap.add_argument("--horizon", type=int, default=None,

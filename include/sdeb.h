@@ -173,6 +173,27 @@ SDEB_API sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream)
  * The pointer stays valid until sdeb_destroy. */
 SDEB_API sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *bytes);
 
+/* Choose the lane-group layout of the context's kernels: each orbit is
+ * integrated by `lanes_per_orbit` consecutive lanes (1, 2, 4, 8, 16 or 32),
+ * each lane owning `units_per_lane` coupling units (a multiple of 4 when
+ * lanes_per_orbit > 1).  Results depend on the layout only through the
+ * order of the coupling sums, so the layout is fixed before the first
+ * integration after sdeb_set_params (ESTATE otherwise) and kept for the
+ * adjoint.  EINVAL if lanes x units does not cover the orbit's units,
+ * EUNSUPPORTED if the model has no kernel for that layout.  sdeb_create
+ * picks a default; sdeb_autotune times the candidates. */
+SDEB_API sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int32_t units_per_lane);
+SDEB_API sdeb_status sdeb_get_layout(const sdeb_ctx *ctx, int32_t *lanes_per_orbit, int32_t *units_per_lane);
+
+/* Layout tuner (motivated by the hand-tuned work-group sizes of the paper's
+ * Table 4): times the forward kernel over the first trial_steps steps
+ * (<= 0: 64) for every instantiated layout that covers the orbit's units
+ * with at most 2x padding, on private copies of the current state, and keeps
+ * the fastest.  Call after sdeb_set_params and before integrating (ESTATE
+ * otherwise).  The context's state, frames and checkpoints are untouched.
+ * Allocates and frees temporary device buffers; synchronises `stream`. */
+SDEB_API sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream);
+
 SDEB_API const char *sdeb_last_error(const sdeb_ctx *ctx);
 SDEB_API const char *sdeb_status_string(sdeb_status s);
 

@@ -23,7 +23,7 @@ __all__ = [
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
-    "sdeb_integrate_noalloc", "model_shape", "EXPORTED_SYMBOLS",
+    "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "model_shape", "EXPORTED_SYMBOLS",
 ]
 
 SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
@@ -98,6 +98,9 @@ _SIGS = {
                                 ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "sdeb_order_param": (_ST, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "sdeb_integrate_noalloc": (_ST, [ctypes.POINTER(Problem), _P, _P, _P, _P, _P]),
+    "sdeb_set_layout": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "sdeb_get_layout": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "sdeb_autotune": (_ST, [_P, ctypes.c_int64, _P]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -180,6 +183,20 @@ def sdeb_frames_device_ptr(ctx):
     p, b = _P(), ctypes.c_size_t()
     _check(lib().sdeb_frames_device_ptr(ctx, ctypes.byref(p), ctypes.byref(b)), ctx)
     return p.value, b.value
+
+
+def sdeb_set_layout(ctx, lanes_per_orbit, units_per_lane):
+    _check(lib().sdeb_set_layout(ctx, lanes_per_orbit, units_per_lane), ctx)
+
+
+def sdeb_autotune(ctx, trial_steps=0, stream=None):
+    _check(lib().sdeb_autotune(ctx, trial_steps, _stream(stream)), ctx)
+
+
+def sdeb_get_layout(ctx):
+    g, p = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sdeb_get_layout(ctx, ctypes.byref(g), ctypes.byref(p)), ctx)
+    return g.value, p.value
 
 
 def sdeb_last_error(ctx=None):

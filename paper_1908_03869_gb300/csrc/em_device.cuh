@@ -160,28 +160,49 @@ __device__ __forceinline__ void box_muller<double>(uint32_t a, uint32_t b, doubl
 // Phase sine / cosine
 // ---------------------------------------------------------------------------
 
-// FP32: the phase is x - c (state minus its Kahan compensation word).
-// q = nearest integer to x / (2 pi) (by the 1.5 * 2^23 rounding bias, valid
-// for |x| < 2^22), r1 = x - q C1 is exact in one fma (C1 = 2 pi rounded to
-// float; for q != 0 both x and q C1 have their lowest bit at or above 2^-22
-// while |r1| < 4), then r = r1 - q C2 - c.
-__device__ __forceinline__ void sincos_phase(float x, float c_comp, float &s, float &c) {
+// FP32: the phase is x - c (state minus its Kahan compensation word),
+// reduced to [-pi, pi] before the SFU.  q = nearest integer to x / (2 pi)
+// (by the 1.5 * 2^23 rounding bias, valid for |x| < 2^22), r1 = x - q C1 is
+// exact in one fma (C1 = 2 pi rounded to float; for q != 0 both x and q C1
+// have their lowest bit at or above 2^-22 while |r1| < 4), then
+// r = r1 - q C2 - c.
+__device__ __forceinline__ float reduce_phase(float x, float c_comp) {
     const float kInv2Pi = 0x1.45f306p-3f;
     const float kC1 = 0x1.921fb6p+2f;
     const float kC2 = -0x1.777a5cp-23f;
     float q = __fmaf_rn(x, kInv2Pi, 12582912.0f) - 12582912.0f;
     float r = __fmaf_rn(-q, kC1, x);
-    r = __fmaf_rn(-q, kC2, r) - c_comp;
-    __sincosf(r, &s, &c);
+    return __fsub_rn(__fmaf_rn(-q, kC2, r), c_comp);
+}
+
+// FP64 keeps the phase unreduced; sin/cos are CUDA's double functions.
+__device__ __forceinline__ double reduce_phase(double x, double c_comp) { return x - c_comp; }
+
+__device__ __forceinline__ void sincos_reduced(float r, float &s, float &c) { __sincosf(r, &s, &c); }
+__device__ __forceinline__ void sincos_reduced(double r, double &s, double &c) { sincos(r, &s, &c); }
+
+__device__ __forceinline__ void sincos_phase(float x, float c_comp, float &s, float &c) {
+    sincos_reduced(reduce_phase(x, c_comp), s, c);
 }
 
 __device__ __forceinline__ void sincos_phase(float x, float &s, float &c) { sincos_phase(x, 0.0f, s, c); }
 
 __device__ __forceinline__ void sincos_phase(double x, double c_comp, double &s, double &c) {
-    sincos(x - c_comp, &s, &c);
+    sincos_reduced(reduce_phase(x, c_comp), s, c);
 }
 
 __device__ __forceinline__ void sincos_phase(double x, double &s, double &c) { sincos(x, &s, &c); }
+
+// ---------------------------------------------------------------------------
+// Explicitly rounded arithmetic: the model increments use these so the
+// compiler has no contraction choice left and every kernel that steps the
+// same model (forward, adjoint replay) produces identical bits.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
 
 // ---------------------------------------------------------------------------
 // Sums over the G consecutive lanes of one orbit.  With a butterfly every

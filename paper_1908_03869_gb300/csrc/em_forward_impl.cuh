@@ -66,10 +66,12 @@ __device__ __forceinline__ void store_units(Real *row, int units, int u0, const 
 // One step of Eq. 2 for the lane's units: coupling sums over the group, then
 // per noise block one Philox call (counter (k, block, orbit, 0)), Box-Muller,
 // and the compensated update of every unit of the block.  Every unit's
-// increment reads only the old state (synchronous update).
-template <class M, typename Real, int G, int P>
+// increment reads only the old state (synchronous update).  With RECORD the
+// normals of the step are also written to zout (the adjoint's replay).
+template <class M, typename Real, int G, int P, bool RECORD = false>
 __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], uint32_t k,
-                                        uint32_t orbit, int u0, int units, const PhiloxKeys &keys) {
+                                        uint32_t orbit, int u0, int units, const PhiloxKeys &keys,
+                                        Real (*zout)[P] = nullptr) {
     constexpr int NRA = M::NR > 0 ? M::NR : 1;
     Real red[NRA];
     model.prepare(x, cp, u0, units, red);
@@ -93,6 +95,7 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
                 model.incr(i, x, red, z[q], inc);
 #pragma unroll
                 for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
+                if constexpr (RECORD) (*zout)[i] = z[q];
             }
         }
     }

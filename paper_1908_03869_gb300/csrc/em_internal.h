@@ -53,6 +53,30 @@ cudaError_t launch_forward_kuramoto_f64(const ForwardArgs &a, Layout l, cudaStre
 cudaError_t launch_forward_other_f32(const ForwardArgs &a, Layout l, cudaStream_t s);
 cudaError_t launch_forward_other_f64(const ForwardArgs &a, Layout l, cudaStream_t s);
 
+// Arguments of the discrete-adjoint launch (Kuramoto models).
+struct AdjointArgs {
+    int32_t model;
+    int32_t n, units, d;
+    int64_t orbits;
+    const void *params;
+    int64_t param_stride;
+    const void *ckpt;          // [C+1][orbits][n], checkpoint c = state at step c*ckpt_every
+    const float *ckpt_comp;    // FP32 compensation at the checkpoints
+    uint32_t ckpt_every, steps;
+    uint32_t orbit_offset;
+    double dt;
+    void *seg;                 // [ckpt_every][orbits][2n] replayed phases and normals (scratch)
+    const void *dL_dxK;        // [orbits][n]
+    void *dL_dp;               // [orbits][d]
+    void *dL_dx0;              // [orbits][n] or nullptr
+    PhiloxKeys keys;
+};
+
+cudaError_t launch_adjoint(const AdjointArgs &a, Layout l, bool fp64, cudaStream_t s);
+// out[q] = sum over orbits of in[o][q], in a fixed order (deterministic).
+cudaError_t launch_sum_over_orbits(const void *in, int64_t orbits, int32_t d, bool fp64, void *out,
+                                   cudaStream_t s);
+
 // Default layout for a number of units (smallest lane group holding them).
 inline bool default_layout(int units, Layout &l) {
     if (units <= 1) l = {1, 1};

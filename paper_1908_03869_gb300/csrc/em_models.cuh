@@ -66,9 +66,9 @@ struct KuramotoLane {
     __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&red)[NR], Real N,
                                          Real (&inc)[U]) const {
         (void)x;
-        Real coupling = red[1] * cs[i] - red[0] * sn[i];
-        Real f = omega[i] + kn * coupling;
-        inc[0] = f * dt + gsq[PAPER ? i : 0] * N;
+        const Real coupling = fma_r(red[1], cs[i], -mul_r(red[0], sn[i]));  // S cos - C sin
+        const Real f = fma_r(kn, coupling, omega[i]);
+        inc[0] = fma_r(f, dt, mul_r(gsq[PAPER ? i : 0], N));
     }
 };
 

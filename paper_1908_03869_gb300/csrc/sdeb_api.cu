@@ -29,6 +29,8 @@ struct sdeb_ctx {
     float *d_ckpt_comp = nullptr;
     int64_t nckpt = 0;
     uint8_t *d_flags = nullptr;
+    void *d_seg = nullptr;        // adjoint: replayed phases and normals of one segment
+    void *d_gradp = nullptr;      // adjoint: per-orbit parameter gradients (shared params)
     bool params_set = false;
     int64_t k_current = 0;
     std::string err;
@@ -86,6 +88,9 @@ void free_buffers(sdeb_ctx *c) {
     cudaFree(c->d_ckpt);
     cudaFree(c->d_ckpt_comp);
     cudaFree(c->d_flags);
+    cudaFree(c->d_seg);
+    cudaFree(c->d_gradp);
+    c->d_seg = c->d_gradp = nullptr;
     c->d_params = c->d_x = c->d_frames = c->d_ckpt = nullptr;
     c->d_comp = c->d_ckpt_comp = nullptr;
     c->d_flags = nullptr;
@@ -119,6 +124,20 @@ sdeb_status validate(const sdeb_problem *pb, int32_t &units) {
     if (!default_layout(units, l))
         return fail(nullptr, SDEB_EUNSUPPORTED, "more than 256 units per orbit is not supported");
     return SDEB_OK;
+}
+
+// Layouts with a forward kernel for the model (and, for the Kuramoto models,
+// an adjoint kernel): the default set for every model, the tuning set for
+// the phase models.
+bool layout_instantiated(int32_t model, Layout l) {
+    static const Layout kDefault[] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 8}, {4, 8}, {8, 8}, {16, 8}, {32, 8}};
+    static const Layout kTuning[] = {{2, 4}, {4, 4}, {8, 4}, {16, 4}, {32, 4}, {4, 16}, {8, 16}};
+    for (const Layout &d : kDefault)
+        if (d.G == l.G && d.P == l.P) return true;
+    if (model == SDEB_KURAMOTO)
+        for (const Layout &d : kTuning)
+            if (d.G == l.G && d.P == l.P) return true;
+    return false;
 }
 
 cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream_t s) {
@@ -163,12 +182,15 @@ sdeb_status sdeb_create(const sdeb_problem *pb, sdeb_ctx **out) {
 
     const size_t elem = pb->precision == SDEB_FP64 ? 8 : 4;
     const bool shared = pb->flags & SDEB_FLAG_SHARED_PARAMS;
-    int64_t state_elems, param_elems, frame_elems = 0, ckpt_elems = 0;
+    int64_t state_elems, param_elems, frame_elems = 0, ckpt_elems = 0, seg_elems = 0, gradp_elems = 0;
+    const bool adjoint = pb->ckpt_every > 0 && (pb->model == SDEB_KURAMOTO || pb->model == SDEB_KURAMOTO_PAPER);
     int64_t nframes = (pb->flags & SDEB_FLAG_NO_FRAMES) ? 0 : pb->steps / pb->stride + 1;
     int64_t nckpt = pb->ckpt_every > 0 ? (pb->steps + pb->ckpt_every - 1) / pb->ckpt_every + 1 : 0;
     if (!mul_ok(pb->orbits, pb->n, state_elems) || !mul_ok(shared ? 1 : pb->orbits, pb->d, param_elems) ||
         !mul_ok(nframes, state_elems, frame_elems) || !mul_ok(nckpt, state_elems, ckpt_elems) ||
-        frame_elems > INT64_MAX / 8 || ckpt_elems > INT64_MAX / 8)
+        !mul_ok(adjoint ? 2 * (int64_t)pb->ckpt_every : 0, state_elems, seg_elems) ||
+        !mul_ok(adjoint && shared ? pb->orbits : 0, pb->d, gradp_elems) ||
+        frame_elems > INT64_MAX / 8 || ckpt_elems > INT64_MAX / 8 || seg_elems > INT64_MAX / 8)
         return fail(nullptr, SDEB_EINVAL, "problem size overflows");
 
     sdeb_ctx *c = new (std::nothrow) sdeb_ctx;
@@ -198,6 +220,8 @@ sdeb_status sdeb_create(const sdeb_problem *pb, sdeb_ctx **out) {
         {&c->d_ckpt, (size_t)ckpt_elems * elem, "checkpoints"},
         {(void **)&c->d_ckpt_comp, elem == 4 ? (size_t)ckpt_elems * 4 : 0, "checkpoint compensation"},
         {(void **)&c->d_flags, (size_t)pb->orbits, "flags"},
+        {&c->d_seg, (size_t)seg_elems * elem, "adjoint segment buffer"},
+        {&c->d_gradp, (size_t)gradp_elems * elem, "per-orbit gradients"},
     };
     for (auto &a : allocs) {
         if (a.bytes == 0) continue;
@@ -357,6 +381,104 @@ sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream) {
     return SDEB_OK;
 }
 
+sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int32_t units_per_lane) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    const int G = lanes_per_orbit, P = units_per_lane;
+    if (!(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32) || P < 1 || P > 16 ||
+        (G > 1 && P % 4 != 0) || (int64_t)G * P < ctx->units)
+        return fail(ctx, SDEB_EINVAL, "layout G=%d P=%d invalid for %d units", G, P, ctx->units);
+    if (ctx->params_set && ctx->k_current != 0)
+        return fail(ctx, SDEB_ESTATE, "set the layout before integrating");
+    if (!layout_instantiated(ctx->pb.model, {G, P}))
+        return fail(ctx, SDEB_EUNSUPPORTED, "no kernel for model %d with G=%d P=%d", ctx->pb.model, G, P);
+    ctx->layout = {G, P};
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (!ctx->params_set || ctx->k_current != 0)
+        return fail(ctx, SDEB_ESTATE, "call sdeb_autotune after sdeb_set_params and before integrating");
+    if (trial_steps <= 0) trial_steps = 64;
+    if (trial_steps > ctx->pb.steps) trial_steps = ctx->pb.steps;
+    if (trial_steps == 0) return SDEB_OK;
+    static const Layout kCandidates[] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 4}, {2, 8}, {4, 4}, {4, 8}, {4, 16},
+                                         {8, 4}, {8, 8}, {8, 16}, {16, 4}, {16, 8}, {32, 4}, {32, 8}};
+    const cudaStream_t s = as_stream(stream);
+    const size_t state_bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
+    void *tx = nullptr;
+    float *tc = nullptr;
+    uint8_t *tf = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&tx, state_bytes);
+    if (e == cudaSuccess && ctx->d_comp) e = cudaMalloc((void **)&tc, (size_t)ctx->pb.orbits * ctx->pb.n * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&tf, (size_t)ctx->pb.orbits);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    Layout best = ctx->layout;
+    float best_ms = 1e30f;
+    for (const Layout &l : kCandidates) {
+        if (e != cudaSuccess) break;
+        // lanes x units must cover the orbit and waste at most half of it
+        const int64_t cover = (int64_t)l.G * l.P;
+        if (cover < ctx->units || (cover > 4 && cover > 2 * (int64_t)ctx->units)) continue;
+        if (!layout_instantiated(ctx->pb.model, l)) continue;
+        ForwardArgs a{};
+        a.model = ctx->pb.model;
+        a.n = ctx->pb.n;
+        a.units = ctx->units;
+        a.orbits = ctx->pb.orbits;
+        a.params = ctx->d_params;
+        a.param_stride = (ctx->pb.flags & SDEB_FLAG_SHARED_PARAMS) ? 0 : ctx->pb.d;
+        a.x = tx;
+        a.comp = tc;
+        a.k_begin = 0;
+        a.k_end = (uint32_t)trial_steps;
+        a.stride = (uint32_t)ctx->pb.stride;
+        a.orbit_offset = (uint32_t)ctx->pb.orbit_offset;
+        a.dt = ctx->pb.dt;
+        a.flags = tf;
+        a.keys = philox_key_schedule(ctx->pb.seed);
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
+            e = cudaMemcpyAsync(tx, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess && tc) e = cudaMemsetAsync(tc, 0, (size_t)ctx->pb.orbits * ctx->pb.n * 4, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch_forward(a, l, ctx->pb.precision == SDEB_FP64, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e == cudaErrorNotSupported) {
+            e = cudaSuccess;
+            cudaGetLastError();
+            continue;
+        }
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = l;
+        }
+    }
+    cudaFree(tx);
+    cudaFree(tc);
+    cudaFree(tf);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sdeb_autotune");
+    }
+    ctx->layout = best;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_get_layout(const sdeb_ctx *ctx, int32_t *lanes_per_orbit, int32_t *units_per_lane) {
+    if (!ctx || !lanes_per_orbit || !units_per_lane) return fail(nullptr, SDEB_EINVAL, "NULL argument");
+    *lanes_per_orbit = ctx->layout.G;
+    *units_per_lane = ctx->layout.P;
+    return SDEB_OK;
+}
+
 sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *bytes) {
     if (!ctx || !ptr || !bytes) return fail(ctx, SDEB_EINVAL, "NULL argument");
     *ptr = ctx->d_frames;
@@ -365,9 +487,42 @@ sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *bytes) {
 }
 
 sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_dx0, void *stream) {
-    (void)dL_dxK; (void)dL_dp; (void)dL_dx0; (void)stream;
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
-    return fail(ctx, SDEB_EUNSUPPORTED, "adjoint not available");
+    if (!dL_dxK || !dL_dp) return fail(ctx, SDEB_EINVAL, "dL_dxK and dL_dp must not be NULL");
+    if (ctx->pb.model != SDEB_KURAMOTO && ctx->pb.model != SDEB_KURAMOTO_PAPER)
+        return fail(ctx, SDEB_EUNSUPPORTED, "the adjoint is implemented for the Kuramoto models");
+    if (ctx->pb.ckpt_every <= 0) return fail(ctx, SDEB_ESTATE, "context was created with ckpt_every = 0");
+    if (!ctx->params_set || ctx->k_current != ctx->pb.steps)
+        return fail(ctx, SDEB_ESTATE, "integrate to step %lld first (state is at %lld)", (long long)ctx->pb.steps,
+                    (long long)ctx->k_current);
+    const bool shared = ctx->pb.flags & SDEB_FLAG_SHARED_PARAMS;
+    AdjointArgs a{};
+    a.model = ctx->pb.model;
+    a.n = ctx->pb.n;
+    a.units = ctx->units;
+    a.d = ctx->pb.d;
+    a.orbits = ctx->pb.orbits;
+    a.params = ctx->d_params;
+    a.param_stride = shared ? 0 : ctx->pb.d;
+    a.ckpt = ctx->d_ckpt;
+    a.ckpt_comp = ctx->d_ckpt_comp;
+    a.ckpt_every = (uint32_t)ctx->pb.ckpt_every;
+    a.steps = (uint32_t)ctx->pb.steps;
+    a.orbit_offset = (uint32_t)ctx->pb.orbit_offset;
+    a.dt = ctx->pb.dt;
+    a.seg = ctx->d_seg;
+    a.dL_dxK = dL_dxK;
+    a.dL_dp = shared ? ctx->d_gradp : dL_dp;
+    a.dL_dx0 = dL_dx0;
+    a.keys = philox_key_schedule(ctx->pb.seed);
+    const bool fp64 = ctx->pb.precision == SDEB_FP64;
+    const cudaStream_t s = as_stream(stream);
+    cudaError_t e = launch_adjoint(a, ctx->layout, fp64, s);
+    if (e == cudaErrorNotSupported)
+        return fail(ctx, SDEB_EUNSUPPORTED, "no adjoint kernel for layout G=%d P=%d", ctx->layout.G, ctx->layout.P);
+    if (e == cudaSuccess && shared) e = launch_sum_over_orbits(ctx->d_gradp, ctx->pb.orbits, ctx->pb.d, fp64, dL_dp, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
+    return SDEB_OK;
 }
 
 sdeb_status sdeb_philox_fill(uint64_t seed, uint32_t k0, int64_t nk, uint32_t b0, int64_t nb, uint32_t o0,

@@ -8,9 +8,9 @@ import ctypes
 
 import torch
 
-from . import (SDEB_FLAG_NO_FRAMES, SDEB_FLAG_SHARED_PARAMS, SDEB_FP64, Problem, sdeb_create, sdeb_destroy,
-               sdeb_grad, sdeb_integrate, sdeb_integrate_range, sdeb_orbit_flags, sdeb_read_final,
-               sdeb_read_orbits, sdeb_set_params)
+from . import (SDEB_FLAG_NO_FRAMES, SDEB_FLAG_SHARED_PARAMS, SDEB_FP64, Problem, sdeb_autotune, sdeb_create,
+               sdeb_destroy, sdeb_get_layout, sdeb_grad, sdeb_integrate, sdeb_integrate_range, sdeb_orbit_flags,
+               sdeb_read_final, sdeb_read_orbits, sdeb_set_layout, sdeb_set_params)
 
 
 def _ptr(t):
@@ -63,6 +63,17 @@ class Integrator:
         params, x0 = params.contiguous(), x0.contiguous()
         self._keep = (params, x0)  # device copies are stream-ordered: keep the sources alive
         sdeb_set_params(self.ctx, _ptr(params), _ptr(x0), params.is_cuda, self._stream(stream))
+
+    def set_layout(self, lanes_per_orbit, units_per_lane):
+        sdeb_set_layout(self.ctx, lanes_per_orbit, units_per_lane)
+
+    def layout(self):
+        return sdeb_get_layout(self.ctx)
+
+    def autotune(self, trial_steps=0, stream=None):
+        """Pick the fastest lane-group layout (after set_params, before integrating)."""
+        sdeb_autotune(self.ctx, trial_steps, self._stream(stream))
+        return self.layout()
 
     def integrate(self, stream=None):
         sdeb_integrate(self.ctx, self._stream(stream))

@@ -1,0 +1,195 @@
+"""GPU parity of the discrete adjoint (sdeb_grad) and the order parameter.
+
+* Per-orbit gradients dL/dp and dL/dx0 against the FP64 oracle adjoint
+  (dense Jacobians, all states stored) on the same inputs and the same
+  dL/dX^K: FP64 to 1e-10 and FP32 to 1e-3, relative to the largest gradient
+  component of the orbit; ragged segments (steps not a multiple of
+  ckpt_every), both parameter layouts, several lane-group layouts.
+* The adjoint workload (n = 32, 16384 orbits sharing one parameter vector,
+  dt = 0.01, 2000 steps, checkpoints every 100, loss = mean order parameter
+  at T = 20): the FP64 adjoint against central finite differences of the
+  FP64 forward with common random numbers (T = 5 and T = 20).  FP32 against
+  FP64: the orbit-mean gradient to 1e-3 at T = 5; at T = 20 the mean is
+  carried by the ~1 % of orbits whose pathwise gradients explode (orbits
+  near the synchronisation transition, where the FP32 and FP64 trajectories
+  themselves part), so there the check is per orbit: the median orbit agrees
+  to 1e-4 and fewer than 5 % of orbits differ by more than 1e-3.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1908_03869_gb300 as sdeb
+from paper_1908_03869_gb300 import build as sdeb_build
+from paper_1908_03869_gb300 import inputs
+
+from helpers import np_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sdeb_build.build()
+    sdeb.lib()
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    scale = np.maximum(np.abs(b).max(axis=-1, keepdims=True), 1e-300)
+    return float((np.abs(a - b) / scale).max())
+
+
+def _gpu_grad(model, n, p, x0, dt, steps, ckpt, seed, precision, dL_dxK, shared=False):
+    import torch
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    dt_t = torch.float64 if precision == "fp64" else torch.float32
+    pb = sdeb.Problem.make(model, n, x0.shape[0], dt, steps, 1, seed, precision, ckpt_every=ckpt,
+                           no_frames=True, shared_params=shared)
+    with Integrator(pb) as it:
+        it.set_params(torch.tensor(p, dtype=dt_t).cuda(), torch.tensor(x0, dtype=dt_t).cuda())
+        it.integrate()
+        xK = it.final().cpu().numpy()
+        dp, dx0 = it.grad(torch.tensor(dL_dxK, dtype=dt_t).cuda())
+        torch.cuda.synchronize()
+        return xK, dp.cpu().numpy(), dx0.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("model,n,ckpt", [("kuramoto", 3, 37), ("kuramoto", 8, 50), ("kuramoto", 32, 64),
+                                          ("kuramoto", 20, 300), ("kuramoto_paper", 12, 41),
+                                          ("kuramoto", 128, 100)])
+def test_adjoint_matches_oracle(precision, model, n, ckpt):
+    orbits, dt, steps, seed = 9, 0.01, 300, 4
+    if model == "kuramoto":
+        p, x0 = inputs.kuramoto(n, orbits, seed=n)
+    else:
+        p, x0 = inputs.kuramoto_paper_speed(n, orbits, seed=n)
+        p[:, 0] = 2.0
+        p[:, n + 1:] = 0.3
+    p, x0 = p.astype(np_dtype(precision)).astype(np.float64), x0.astype(np_dtype(precision)).astype(np.float64)
+    c = np.random.Generator(np.random.PCG64(n)).standard_normal((orbits, n))
+    _, dp, dx0 = _gpu_grad(model, n, p, x0, dt, steps, ckpt, seed, precision, c)
+    m, d = sdeb.model_shape(model, n)
+    pb = oracle.make_problem(model, n, m, d, dt, steps, 1, seed)
+    rdp, rdx0 = oracle.adjoint(pb, p, x0, c)
+    tol = 1e-10 if precision == "fp64" else 1e-3
+    assert _rel(dp, rdp) < tol
+    assert _rel(dx0, rdx0) < tol
+
+
+def _loss_and_grads(precision, p, x0, W, steps=None, want_grad=True, shared=True):
+    import torch
+    from paper_1908_03869_gb300.autograd import integrate_final, order_parameter
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    dt_t = torch.float64 if precision == "fp64" else torch.float32
+    n, orbits = x0.shape[1], x0.shape[0]
+    pb = sdeb.Problem.make("kuramoto", n, orbits, W["dt"], steps or W["steps"], 1, W["seed"], precision,
+                           ckpt_every=W["ckpt_every"], no_frames=True, shared_params=shared)
+    with Integrator(pb) as it:
+        pt = torch.tensor(p, dtype=dt_t, device="cuda", requires_grad=want_grad)
+        xt = torch.tensor(x0, dtype=dt_t, device="cuda")
+        loss = order_parameter(integrate_final(it, pt, xt)).mean()
+        if want_grad:
+            loss.backward()
+            return float(loss.detach()), pt.grad.cpu().numpy().astype(np.float64)
+        return float(loss), None
+
+
+@pytest.mark.parametrize("steps", [500, 2000])
+def test_adjoint_workload_fp64_vs_central_fd(steps):
+    W = inputs.WORKLOADS["kuramoto_adjoint_n32"]
+    p, x0 = inputs.kuramoto(32, W["orbits"], seed=1, shared=True)
+    _, g64 = _loss_and_grads("fp64", p, x0, W, steps)
+    scale = np.abs(g64).max()
+    # Orbits near the synchronisation transition have pathwise derivatives
+    # ~1e4 times the typical one at T = 20, so the loss is linear in p only
+    # over a small range: the differences use h = 1e-6, 1e-7 and 1e-8
+    # (times max(|p_q|, 1)) and the adjoint must match the best of them.
+    for q in [0, 1, 2, 7, 33]:           # K, sigma and three omegas
+        errs = []
+        for rel_h in (1e-6, 1e-7, 1e-8):
+            h = rel_h * max(abs(p[q]), 1.0)
+            pp, pm = p.copy(), p.copy()
+            pp[q] += h
+            pm[q] -= h
+            Lp, _ = _loss_and_grads("fp64", pp, x0, W, steps, want_grad=False)
+            Lm, _ = _loss_and_grads("fp64", pm, x0, W, steps, want_grad=False)
+            fd = (Lp - Lm) / (2 * h)
+            errs.append(abs(g64[q] - fd) / max(abs(fd), 1e-2 * scale))
+        assert min(errs) < 1e-3, (q, g64[q], errs)
+
+
+def test_adjoint_workload_fp32_vs_fp64():
+    W = inputs.WORKLOADS["kuramoto_adjoint_n32"]
+    orbits = W["orbits"]
+    p, x0 = inputs.kuramoto(32, orbits, seed=1, shared=True)
+    p, x0 = p.astype(np.float32).astype(np.float64), x0.astype(np.float32).astype(np.float64)
+    # T = 5: the orbit mean of the shared-parameter gradient
+    L64, g64 = _loss_and_grads("fp64", p, x0, W, 500)
+    L32, g32 = _loss_and_grads("fp32", p, x0, W, 500)
+    assert abs(L32 - L64) < 1e-5
+    assert np.abs(g32 - g64).max() < 1e-3 * np.abs(g64).max()
+    # T = 20: per-orbit gradients
+    pt = np.tile(p, (orbits, 1))
+    _, G64 = _loss_and_grads("fp64", pt, x0, W, shared=False)
+    _, G32 = _loss_and_grads("fp32", pt, x0, W, shared=False)
+    rel = np.abs(G32 - G64).max(axis=1) / np.abs(G64).max(axis=1)
+    assert np.median(rel) < 1e-4, np.median(rel)
+    assert (rel > 1e-3).mean() < 0.05, (rel > 1e-3).mean()
+
+
+def test_adjoint_workload_sampled_orbits_vs_oracle():
+    """Per-orbit FP64 gradients of the order-parameter loss against the oracle,
+    whose dL/dX^K comes from its own final state."""
+    import torch
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    W = inputs.WORKLOADS["kuramoto_adjoint_n32"]
+    n, orbits = 32, W["orbits"]
+    p, x0 = inputs.kuramoto(n, orbits, seed=1, shared=True)
+    sample = [0, 1, 777, 4095, 16383]
+    pb = sdeb.Problem.make("kuramoto", n, orbits, W["dt"], W["steps"], 1, W["seed"], "fp64",
+                           ckpt_every=W["ckpt_every"], no_frames=True)   # per-orbit gradients
+    pfull = np.tile(p, (orbits, 1))
+    with Integrator(pb) as it:
+        it.set_params(torch.tensor(pfull).cuda(), torch.tensor(x0).cuda())
+        it.integrate()
+        xK = it.final()
+        r = torch.empty(orbits, dtype=torch.float64, device="cuda")
+        dr = torch.empty_like(xK)
+        sdeb.sdeb_order_param(ctypes.c_void_p(xK.data_ptr()), orbits, n, sdeb.SDEB_FP64,
+                              ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(dr.data_ptr()))
+        dp, dx0 = it.grad(dr / orbits)
+        dp, dx0, xK = dp.cpu().numpy(), dx0.cpu().numpy(), xK.cpu().numpy()
+    opb = oracle.make_problem("kuramoto", n, n, n + 2, W["dt"], W["steps"], 1, W["seed"])
+    for o in sample:
+        _, oxK = oracle.integrate(opb, pfull[o:o + 1], x0[o:o + 1], orbit_begin=o, frames=False)
+        _, odr = oracle.order_param(oxK[0])
+        rdp, rdx0 = oracle.adjoint(opb, pfull[o:o + 1], x0[o:o + 1], (odr / orbits)[None, :], orbit_begin=o)
+        assert _rel(dp[o:o + 1], rdp) < 1e-8, o
+        assert _rel(dx0[o:o + 1], rdx0) < 1e-8, o
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_order_param_kernel(precision):
+    import torch
+    th = np.random.Generator(np.random.PCG64(2)).uniform(-50, 50, (300, 37)).astype(np_dtype(precision))
+    dt_t = torch.float64 if precision == "fp64" else torch.float32
+    t = torch.tensor(th, dtype=dt_t, device="cuda")
+    r = torch.empty(300, dtype=dt_t, device="cuda")
+    dr = torch.empty_like(t)
+    sdeb.sdeb_order_param(ctypes.c_void_p(t.data_ptr()), 300, 37, sdeb.PRECISIONS[precision],
+                          ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(dr.data_ptr()))
+    r, dr = r.cpu().numpy(), dr.cpu().numpy()
+    tol = 1e-13 if precision == "fp64" else 2e-5
+    for o in range(300):
+        rr, rdr = oracle.order_param(th[o].astype(np.float64))
+        assert abs(r[o] - rr) < tol
+        assert np.abs(dr[o] - rdr).max() < tol * 10

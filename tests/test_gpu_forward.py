@@ -157,3 +157,41 @@ def test_nonfinite_flag(precision):
         it.integrate()
         flags = it.flags().numpy()
     assert flags.tolist() == [1, 0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_layouts_and_autotune(precision):
+    import torch
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    n, orbits, steps, stride = 32, 301, 200, 50
+    p, x0 = _cast(precision, *inputs.kuramoto(n, orbits, seed=31))
+    rfr, _ = run_oracle("kuramoto", n, p, x0, 0.01, steps, stride, seed=2)
+    dt_t = torch.float64 if precision == "fp64" else torch.float32
+    pt, xt = torch.tensor(p, dtype=dt_t).cuda(), torch.tensor(x0, dtype=dt_t).cuda()
+    for layout in [(4, 8), (8, 4), (2, 16), (16, 4), (4, 16), (32, 4)]:
+        pb = sdeb.Problem.make("kuramoto", n, orbits, 0.01, steps, stride, 2, precision)
+        with Integrator(pb) as it:
+            if layout == (2, 16):
+                with pytest.raises(sdeb.SdebError) as e:      # no kernel for this layout
+                    it.set_layout(*layout)
+                assert e.value.status == sdeb.SDEB_EUNSUPPORTED
+                continue
+            it.set_layout(*layout)
+            assert it.layout() == layout
+            it.set_params(pt, xt)
+            it.integrate()
+            assert max_rel_err(it.frames().cpu().numpy(), rfr) < TOL[precision]
+    pb = sdeb.Problem.make("kuramoto", n, orbits, 0.01, steps, stride, 2, precision)
+    with Integrator(pb) as it:
+        with pytest.raises(sdeb.SdebError) as e:
+            it.set_layout(2, 8)                               # 16 units < 32
+        assert e.value.status == sdeb.SDEB_EINVAL
+        it.set_params(pt, xt)
+        chosen = it.autotune(trial_steps=32)
+        assert chosen[0] * chosen[1] >= n
+        it.integrate()
+        assert max_rel_err(it.frames().cpu().numpy(), rfr) < TOL[precision]
+        with pytest.raises(sdeb.SdebError) as e:
+            it.autotune()
+        assert e.value.status == sdeb.SDEB_ESTATE
