@@ -45,6 +45,10 @@ SFU_OPS_PER_OSC_STEP = 4
 SFU_PER_SM_PER_CLK = 16
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) of one forward launch of the n = 32 problem, from
+# the ncu capture summarised in profiles/em_forward_kuramoto_fp32_n32_dram_full_size.md;
+# set to None whenever the forward kernel changes until it is measured again.
+FORWARD_N32_DRAM_BYTES = 3.50e9
 
 
 def _dist_env():
@@ -175,6 +179,7 @@ def run_ours(args):
     from paper_1908_03869_gb300 import build as sdeb_build
     from paper_1908_03869_gb300 import inputs
     from paper_1908_03869_gb300.integrator import Integrator
+    from paper_1908_03869_gb300.sharding import max_over_ranks, weak_scaling_offset
 
     ws, rank, local = _dist_env()
     if not torch.cuda.is_available():
@@ -196,7 +201,8 @@ def run_ours(args):
     its, dev_inputs, host_inputs = [], [], []
     for n, orbits in CONFIGS:
         p, x0 = inputs.kuramoto(n, orbits, seed=1 + rank)
-        pb = sdeb.Problem.make("kuramoto", n, orbits, DT, STEPS, STRIDE, SEED, "fp32", orbit_offset=rank * orbits)
+        pb = sdeb.Problem.make("kuramoto", n, orbits, DT, STEPS, STRIDE, SEED, "fp32",
+                               orbit_offset=weak_scaling_offset(orbits, rank))
         its.append(Integrator(pb))
         pt, xt = torch.tensor(p, dtype=dtype), torch.tensor(x0, dtype=dtype)
         dev_inputs.append((pt.cuda(), xt.cuda()))
@@ -250,11 +256,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     kern_ms = [[a.elapsed_time(b) for a, b in row] for row in kern_ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, device="cuda")
     value = units_per_step * ws * args.steps / (total_ms / 1e3)
 
     # ---- roofline of the dominant kernel (forward EM, FP32) --------------
@@ -285,11 +287,7 @@ def run_ours(args):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         e2e = {"value": units_per_step * ws * args.steps / e2e_s, "unit": "orbit-steps/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         del host_frames
@@ -301,7 +299,8 @@ def run_ours(args):
         t64, u64 = 0.0, 0
         for n, orbits in CONFIGS:
             p, x0 = inputs.kuramoto(n, orbits, seed=1 + rank)
-            pb = sdeb.Problem.make("kuramoto", n, orbits, DT, steps64, STRIDE, SEED, "fp64", orbit_offset=rank * orbits)
+            pb = sdeb.Problem.make("kuramoto", n, orbits, DT, steps64, STRIDE, SEED, "fp64",
+                                   orbit_offset=weak_scaling_offset(orbits, rank))
             with Integrator(pb) as it64:
                 pt, xt = torch.tensor(p, device="cuda"), torch.tensor(x0, device="cuda")
                 it64.set_params(pt, xt, stream=stream)
@@ -345,7 +344,9 @@ def run_ours(args):
             "wall_s": wall,
             "per_launch_ms": per_launch_ms, "layouts_G_P": layouts,
             "roofline": {"bound": "alu", "pipe": "SFU (MUFU)", "achieved": achieved, "peak": peak,
-                         "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "Gop/s", "frac": achieved / peak,
+                         "traffic": FORWARD_N32_DRAM_BYTES if args.orbit_scale == 1.0 and args.horizon is None else None,
+                         "traffic_note": "DRAM bytes of the n=32 launch (ncu); algorithmic 3.52e9",
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
             "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "cpu_baseline": cpu, "clocks": clk,
@@ -373,7 +374,7 @@ def _time_adjoint(stream, rank, reps=5):
     xt = torch.tensor(x0, dtype=torch.float32, device="cuda")
     mk = lambda ck: sdeb.Problem.make("kuramoto", n, orbits, W["dt"], W["steps"], 1, W["seed"], "fp32",
                                       ckpt_every=ck, no_frames=True, shared_params=True,
-                                      orbit_offset=rank * orbits)
+                                      orbit_offset=weak_scaling_offset(orbits, rank))
     ev = lambda: torch.cuda.Event(enable_timing=True)
     with Integrator(mk(0)) as plain, Integrator(mk(W["ckpt_every"])) as ck:
         # dL/dX^K of the mean order parameter at T, from the library's kernel
