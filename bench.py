@@ -322,6 +322,11 @@ def run_ours(args):
     if not args.no_adjoint:
         adjoint = _time_adjoint(stream, rank)
 
+    # ---- batched heterogeneous instances (one persistent graph launch) -----
+    batched = None
+    if not args.no_batched:
+        batched = _time_batch(stream, rank)
+
     # ---- CPU oracle on this host's cores --------------------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -349,13 +354,51 @@ def run_ours(args):
                          "traffic_note": "DRAM bytes of the n=32 launch (ncu); algorithmic 3.52e9",
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
-            "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _time_batch(stream, rank, reps=5):
+    import numpy as np
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import BatchIntegrator
+
+    W = inputs.WORKLOADS["batched_4096"]
+    insts = inputs.batched_instances(W["count"], seed=1)
+    base = rank * W["count"]
+    pbs = [sdeb.Problem.make("kuramoto", d["n"], 1, d["dt"], d["steps"], W["stride"], W["seed"], "fp32",
+                             orbit_offset=base + i) for i, d in enumerate(insts)]
+    ps = [d["params"][None, :].astype(np.float32) for d in insts]
+    xs = [d["x0"][None, :].astype(np.float32) for d in insts]
+    orbit_steps = sum(d["steps"] for d in insts)
+    osc_steps = sum(d["steps"] * d["n"] for d in insts)
+    times = []
+    with BatchIntegrator(pbs) as b:
+        b.set_params(ps, xs, stream=stream)
+        info = b.autotune(stream=stream)
+        for _ in range(reps + 1):
+            b.set_params(ps, xs, stream=stream)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b.integrate(stream=stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(e))
+    ms = statistics.median(times[1:])
+    peak = SFU_PER_SM_PER_CLK * NUM_SMS * SM_MAX_MHZ * 1e6
+    longest = max(d["steps"] * d["n"] for d in insts)
+    return {"workload": "4096 Kuramoto instances, n~U{2..256}, steps~logU[1e3,1e5], dt in {0.001,0.01}, stride 100, fp32",
+            "ms": ms, "orbit_steps_per_sec": orbit_steps / (ms / 1e3), "osc_steps_per_sec": osc_steps / (ms / 1e3),
+            "sfu_roofline_frac": SFU_OPS_PER_OSC_STEP * osc_steps / (ms / 1e3) / peak,
+            "total_osc_steps": osc_steps, "longest_instance_osc_steps": longest, "schedule": info}
 
 
 def _time_adjoint(stream, rank, reps=5):
@@ -366,6 +409,7 @@ def _time_adjoint(stream, rank, reps=5):
     import paper_1908_03869_gb300 as sdeb
     from paper_1908_03869_gb300 import inputs
     from paper_1908_03869_gb300.integrator import Integrator
+    from paper_1908_03869_gb300.sharding import weak_scaling_offset
 
     W = inputs.WORKLOADS["kuramoto_adjoint_n32"]
     n, orbits = W["n"], W["orbits"]
@@ -430,6 +474,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--orbit-scale", type=float, default=1.0,
                     help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
     ap.add_argument("--horizon", type=int, default=None,

@@ -121,6 +121,48 @@ typedef struct sdeb_ctx sdeb_ctx;   /* opaque, library-owned */
  * (EINVAL before any CUDA call; ENOMEM / ECUDA afterwards). */
 SDEB_API sdeb_status sdeb_create(const sdeb_problem *pb, sdeb_ctx **out);
 
+/* A batch of heterogeneous problems integrated together by one persistent,
+ * CUDA-graph-launched kernel (the many parameter combinations of the
+ * paper's optimisation use, Sec. 1.2; the work sizing replaces the
+ * hand-tuned work-group sizes of Table 4).  Each pbs[i] is validated as by
+ * sdeb_create; all must be SDEB_KURAMOTO with the same precision and seed
+ * and ckpt_every = 0 (EUNSUPPORTED / EINVAL otherwise), each may have its own
+ * n (<= 256), orbits, t0, dt, steps, stride, flags and orbit_offset (give
+ * every instance distinct global orbit indices so their noise differs).
+ * Buffers are the instances' buffers concatenated in order: sdeb_set_params
+ * takes params = [inst 0 params][inst 1 params]... (each [orbits_i][d_i] or
+ * [d_i] if shared) and x0 = [inst 0 [orbits_i][n_i]]...; sdeb_integrate runs
+ * every instance over its whole horizon (once per sdeb_set_params);
+ * sdeb_batch_read reads one instance; sdeb_orbit_flags returns one byte per
+ * orbit of every instance in order.  sdeb_integrate_range, sdeb_read_orbits,
+ * sdeb_read_final, sdeb_grad and sdeb_set_layout return EUNSUPPORTED;
+ * sdeb_autotune times candidate schedules of the whole batch. */
+SDEB_API sdeb_status sdeb_create_batch(const sdeb_problem *pbs, int32_t count, sdeb_ctx **out);
+
+/* Copy instance `instance` of a batch: what = 0 its frames
+ * [steps_i/stride_i + 1][orbits_i][n_i], what = 1 its final state
+ * [orbits_i][n_i]; dst_bytes exact.  ESTATE before sdeb_integrate. */
+SDEB_API sdeb_status sdeb_batch_read(sdeb_ctx *ctx, int32_t instance, int32_t what, void *dst, size_t dst_bytes,
+                                     int32_t dst_on_device, void *stream);
+
+/* Schedule of a batch: queue tasks, items run as two-warp teams, and the
+ * persistent grid size (blocks of 64 threads). */
+SDEB_API sdeb_status sdeb_batch_info(const sdeb_ctx *ctx, int32_t *tasks, int32_t *team_items, int32_t *grid);
+
+/* Schedule knob of a batch (sdeb_autotune picks it by timing): each orbit
+ * gets the most units per lane (at most 4) whose sequential chain, steps x
+ * per-step cost, stays within chain_fraction x the batch's average work per
+ * SM sub-partition; fewer units per lane spread a long orbit over more lanes
+ * (up to a 128-lane team).  Results depend on the schedule only through the
+ * order of the coupling sums.  EINVAL unless chain_fraction > 0. */
+SDEB_API sdeb_status sdeb_batch_set_schedule(sdeb_ctx *ctx, double chain_fraction);
+
+/* Lane layout the current schedule gives the orbits of `instance`: lanes
+ * per orbit (1..32 within a warp, 64 or 128 for a multi-warp team) and
+ * units per lane.  The orbit's trajectory equals that of a single-problem
+ * context with the same layout (sdeb_set_layout) when lanes <= 32. */
+SDEB_API sdeb_status sdeb_batch_layout(const sdeb_ctx *ctx, int32_t instance, int32_t *lanes, int32_t *units_per_lane);
+
 /* Free the context and its device buffers (synchronises the device first).
  * NULL is accepted. */
 SDEB_API void sdeb_destroy(sdeb_ctx *ctx);

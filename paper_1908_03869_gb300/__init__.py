@@ -23,7 +23,8 @@ __all__ = [
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
-    "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "model_shape", "EXPORTED_SYMBOLS",
+    "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
+    "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "model_shape", "EXPORTED_SYMBOLS",
 ]
 
 SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
@@ -101,6 +102,12 @@ _SIGS = {
     "sdeb_set_layout": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sdeb_get_layout": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sdeb_autotune": (_ST, [_P, ctypes.c_int64, _P]),
+    "sdeb_create_batch": (_ST, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "sdeb_batch_read": (_ST, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.c_int32, _P]),
+    "sdeb_batch_info": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_int32)]),
+    "sdeb_batch_set_schedule": (_ST, [_P, ctypes.c_double]),
+    "sdeb_batch_layout": (_ST, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -191,6 +198,34 @@ def sdeb_set_layout(ctx, lanes_per_orbit, units_per_lane):
 
 def sdeb_autotune(ctx, trial_steps=0, stream=None):
     _check(lib().sdeb_autotune(ctx, trial_steps, _stream(stream)), ctx)
+
+
+def sdeb_create_batch(problems):
+    """problems: a sequence of Problem (or a ctypes array of them)."""
+    arr = (Problem * len(problems))(*problems) if not isinstance(problems, ctypes.Array) else problems
+    ctx = _P()
+    _check(lib().sdeb_create_batch(ctypes.cast(arr, _P), len(arr), ctypes.byref(ctx)))
+    return ctx
+
+
+def sdeb_batch_read(ctx, instance, what, dst, dst_bytes, dst_on_device, stream=None):
+    _check(lib().sdeb_batch_read(ctx, instance, what, dst, dst_bytes, int(dst_on_device), _stream(stream)), ctx)
+
+
+def sdeb_batch_info(ctx):
+    t, tm, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sdeb_batch_info(ctx, ctypes.byref(t), ctypes.byref(tm), ctypes.byref(g)), ctx)
+    return {"tasks": t.value, "team_items": tm.value, "grid": g.value}
+
+
+def sdeb_batch_set_schedule(ctx, chain_fraction):
+    _check(lib().sdeb_batch_set_schedule(ctx, float(chain_fraction)), ctx)
+
+
+def sdeb_batch_layout(ctx, instance):
+    g, p = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sdeb_batch_layout(ctx, instance, ctypes.byref(g), ctypes.byref(p)), ctx)
+    return g.value, p.value
 
 
 def sdeb_get_layout(ctx):

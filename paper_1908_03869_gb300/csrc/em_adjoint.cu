@@ -33,7 +33,7 @@ namespace {
 template <bool PAPER, typename Real, int G, int P>
 __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const AdjointArgs a) {
     using M = KuramotoLane<Real, P, PAPER>;
-    static_assert(G == 1 || P % 4 == 0, "multi-lane orbits need whole noise blocks per lane");
+    static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t orbit = tid / G;
     const int lig = (int)(tid & (G - 1));
@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
 
     const Real *ckpt = static_cast<const Real *>(a.ckpt);
     Real *seg = static_cast<Real *>(a.seg);
+    WarpGroupSum<G> reduce;
     const int64_t nseg = ((int64_t)a.steps + a.ckpt_every - 1) / a.ckpt_every;
 
     for (int64_t c = nseg - 1; c >= 0; --c) {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             Real r[1][P], z[1][P];
 #pragma unroll
             for (int i = 0; i < P; ++i) r[0][i] = reduce_phase(x[0][i], cp[0][i]);
-            em_step<M, Real, G, P, true>(model, x, cp, k, gorb, u0, units, a.keys, &z[0]);
+            em_step<M, Real, P, true>(model, x, cp, k, gorb, u0, units, a.keys, reduce, &z[0]);
             if (active) {
                 Real *row = seg + ((int64_t)(k - k0) * a.orbits + o) * (2 * n);
                 store_units<Real, 1, P>(row, units, u0, r);

@@ -1,0 +1,206 @@
+// Persistent kernel for batches of heterogeneous instances (different n,
+// steps, dt, stride, orbits): the many parameter combinations of the paper's
+// optimisation use (Sec. 1.2) in one launch, scheduled longest-first so the
+// instances with the longest sequential chains start at once.  Work sizing
+// replaces the hand-tuned work-group sizes of the paper's Table 4.
+//
+// Each item (one orbit of one instance) runs Eq. 2 with exactly the step
+// code of the forward kernel (em_step), so an item integrated in a warp task
+// with layout (G, P) is bit-identical to the same orbit in a single-problem
+// context using that layout.  No block ever waits on another: the only
+// shared state is the queue head, advanced with atomicAdd.
+#include "em_forward_impl.cuh"
+
+namespace sdeb {
+
+namespace {
+
+template <typename Real, int P>
+__device__ __forceinline__ void flag_nonfinite(uint8_t *flag, const Real (&x)[1][P], int u0, int units) {
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+        if (u0 + i < units && !isfinite(x[0][i])) bad = true;
+    if (bad) *flag = 1;  // flags start at 0; several lanes may write the same 1
+}
+
+// Integrates one item on the calling lanes: `lane` is the lane's index in the
+// item's lane group, the group sums with `reduce`.  Steps 0..kmax-1 are taken
+// (the group's shuffles or barriers need every lane), the item's own state is
+// stored, framed and flagged only while k < its step count (`live`).
+template <typename Real, int P, class RED>
+__device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it, bool has, int lane, uint32_t kmax,
+                                         RED &reduce) {
+    using M = KuramotoLane<Real, P, false>;
+    constexpr bool kKahan = std::is_same<Real, float>::value;
+    const BatchInstance in = a.inst[it.instance];
+    const int u0 = lane * P;
+    const int units = in.units;
+    const int64_t n = in.n;
+    M model;
+    model.load(static_cast<const Real *>(a.params) + in.p_off + (int64_t)it.orbit * in.param_stride, u0, units,
+               (Real)in.dt, (Real)sqrt(in.dt));
+    Real *xrow = static_cast<Real *>(a.x) + in.x_off + (int64_t)it.orbit * n;
+    float *crow = kKahan ? a.comp + in.x_off + (int64_t)it.orbit * n : nullptr;
+    Real x[1][P], cp[1][P];
+    load_units<Real, 1, P>(xrow, units, u0, x);
+    if constexpr (kKahan) {
+        load_units<float, 1, P>(crow, units, u0, cp);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) cp[0][i] = Real(0);
+    }
+    Real *frames = a.frames != nullptr && in.has_frames ? static_cast<Real *>(a.frames) + in.f_off : nullptr;
+    if (has && frames != nullptr) store_units<Real, 1, P>(frames + (int64_t)it.orbit * n, units, u0, x);
+    const uint32_t gorb = in.orbit_offset + (uint32_t)it.orbit;
+    uint32_t to_frame = in.stride;
+    for (uint32_t k = 0; k < kmax; ++k) {
+        em_step<M, Real, P>(model, x, cp, k, gorb, u0, units, a.keys, reduce);
+        if (has && k < in.steps) {
+            if (--to_frame == 0) {
+                to_frame = in.stride;
+                const int64_t f = (int64_t)((k + 1) / in.stride);
+                if (frames != nullptr)
+                    store_units<Real, 1, P>(frames + (f * in.orbits + it.orbit) * n, units, u0, x);
+            }
+            if (k + 1 == in.steps) {
+                store_units<Real, 1, P>(xrow, units, u0, x);
+                if constexpr (kKahan) store_units<float, 1, P>(crow, units, u0, cp);
+                flag_nonfinite<Real, P>(a.flags + in.o_off + it.orbit, x, u0, units);
+            }
+        }
+    }
+}
+
+template <typename Real, int G, int P>
+__device__ __forceinline__ void run_warp_task(const BatchArgs &a, const BatchWarpTask &t) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane / G;
+    const bool has = g < t.count;
+    WarpGroupSum<G> reduce;
+    run_item<Real, P>(a, a.items[t.first + (has ? g : 0)], has, lane % G, t.kmax, reduce);
+}
+
+template <typename Real>
+__device__ __forceinline__ void run_warp_task_any(const BatchArgs &a, const BatchWarpTask &t) {
+    switch (t.layout) {
+    case 0: run_warp_task<Real, 1, 1>(a, t); break;
+    case 1: run_warp_task<Real, 1, 2>(a, t); break;
+    case 2: run_warp_task<Real, 1, 4>(a, t); break;
+    case 3: run_warp_task<Real, 2, 4>(a, t); break;
+    case 4: run_warp_task<Real, 4, 4>(a, t); break;
+    case 5: run_warp_task<Real, 8, 4>(a, t); break;
+    case 6: run_warp_task<Real, 16, 4>(a, t); break;
+    case 7: run_warp_task<Real, 32, 4>(a, t); break;
+    case 8: run_warp_task<Real, 2, 2>(a, t); break;
+    case 9: run_warp_task<Real, 4, 2>(a, t); break;
+    case 10: run_warp_task<Real, 8, 2>(a, t); break;
+    case 11: run_warp_task<Real, 16, 2>(a, t); break;
+    case 12: run_warp_task<Real, 32, 2>(a, t); break;
+    case 13: run_warp_task<Real, 32, 1>(a, t); break;
+    default: break;
+    }
+}
+
+// Team of NW warps on one item; BAR = 0 is the whole block's barrier,
+// otherwise named barrier BAR for the team's 32 * NW threads.
+template <int NW, int BAR, typename Real>
+struct NamedTeamSum {
+    Real *buf;   // [2][NW][2] in shared memory
+    int flip;
+    int warp0;
+    template <int NR>
+    __device__ __forceinline__ void operator()(Real (&r)[NR]) {
+        static_assert(NR <= 2, "two sums at most");
+        const int warp = (threadIdx.x >> 5) - warp0, lane = threadIdx.x & 31;
+        Real *slot = buf + flip * NW * 2;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            r[q] = group_sum<32>(r[q]);
+            if (lane == 0) slot[warp * 2 + q] = r[q];
+        }
+        if constexpr (BAR == 0) {
+            __syncthreads();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NW * 32) : "memory");
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            Real t = slot[q];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) t += slot[w * 2 + q];
+            r[q] = t;
+        }
+        flip ^= 1;
+    }
+};
+
+template <typename Real, int NW, int P, int BAR>
+__device__ __forceinline__ void run_team(const BatchArgs &a, int32_t item, Real *buf, int warp0) {
+    NamedTeamSum<NW, BAR, Real> reduce{buf, 0, warp0};
+    const BatchItem it = a.items[item];
+    const uint32_t steps = a.inst[it.instance].steps;
+    run_item<Real, P>(a, it, true, (int)threadIdx.x - warp0 * 32, steps, reduce);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kBatchBlock, 6) em_batch_kernel(const BatchArgs a) {
+    __shared__ int s_task;
+    __shared__ Real s_red[2][2 * 4 * 2];
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(a.head, 1);
+        __syncthreads();
+        const int t = s_task;
+        __syncthreads();
+        if (t >= a.ntasks) return;
+        const BatchTask task = a.tasks[t];
+        const int warp = threadIdx.x >> 5;
+        if (task.kind == kBatchWarps) {
+            const BatchWarpTask wt = task.warp[warp];
+            if (wt.count > 0) run_warp_task_any<Real>(a, wt);
+        } else if (task.kind == kBatchTeam128) {
+            if (task.team_p == 1) run_team<Real, 4, 1, 0>(a, task.item[0], s_red[0], 0);
+            else if (task.team_p == 2) run_team<Real, 4, 2, 0>(a, task.item[0], s_red[0], 0);
+            else run_team<Real, 4, 4, 0>(a, task.item[0], s_red[0], 0);
+        } else {
+            const int half = warp >> 1;
+            const int32_t item = task.item[half];
+            if (item >= 0) {
+                if (half == 0) {
+                    if (task.team_p == 1) run_team<Real, 2, 1, 1>(a, item, s_red[0], 0);
+                    else if (task.team_p == 2) run_team<Real, 2, 2, 1>(a, item, s_red[0], 0);
+                    else run_team<Real, 2, 4, 1>(a, item, s_red[0], 0);
+                } else {
+                    if (task.team_p == 1) run_team<Real, 2, 1, 2>(a, item, s_red[1], 2);
+                    else if (task.team_p == 2) run_team<Real, 2, 2, 2>(a, item, s_red[1], 2);
+                    else run_team<Real, 2, 4, 2>(a, item, s_red[1], 2);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch(const BatchArgs &a, int grid, bool fp64, cudaStream_t s) {
+    if (a.ntasks == 0) return cudaSuccess;
+    if (grid < 1) grid = 1;
+    if (fp64)
+        em_batch_kernel<double><<<grid, kBatchBlock, 0, s>>>(a);
+    else
+        em_batch_kernel<float><<<grid, kBatchBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm(bool fp64) {
+    int blocks = 0;
+    cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, em_batch_kernel<double>, kBatchBlock, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, em_batch_kernel<float>, kBatchBlock, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return blocks > 0 ? blocks : 1;
+}
+
+}  // namespace sdeb

@@ -63,41 +63,100 @@ __device__ __forceinline__ void store_units(Real *row, int units, int u0, const 
     }
 }
 
-// One step of Eq. 2 for the lane's units: coupling sums over the group, then
-// per noise block one Philox call (counter (k, block, orbit, 0)), Box-Muller,
-// and the compensated update of every unit of the block.  Every unit's
-// increment reads only the old state (synchronous update).  With RECORD the
-// normals of the step are also written to zout (the adjoint's replay).
-template <class M, typename Real, int G, int P, bool RECORD = false>
+// Coupling-sum reducers.  WarpGroupSum<G>: butterfly over the G lanes of an
+// orbit inside one warp.  TeamSum<NW>: an orbit spread over the NW warps of
+// the whole thread block -- warp butterflies, then the NW partial sums
+// exchanged through shared memory (double-buffered, one barrier per call) and
+// added in warp order, so every lane gets bit-identical totals.
+template <int G>
+struct WarpGroupSum {
+    template <typename Real, int NR>
+    __device__ __forceinline__ void operator()(Real (&r)[NR]) const {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r[q] = group_sum<G>(r[q]);
+    }
+};
+
+template <int NW, typename Real>
+struct TeamSum {
+    Real *buf;  // shared memory, [2][NW][NRMAX]
+    int flip;
+    static constexpr int NRMAX = 2;
+    template <int NR>
+    __device__ __forceinline__ void operator()(Real (&r)[NR]) {
+        static_assert(NR <= NRMAX, "TeamSum holds at most NRMAX sums");
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        Real *slot = buf + flip * NW * NRMAX;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            r[q] = group_sum<32>(r[q]);
+            if (lane == 0) slot[warp * NRMAX + q] = r[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            Real t = slot[q];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) t += slot[w * NRMAX + q];
+            r[q] = t;
+        }
+        flip ^= 1;
+    }
+};
+
+// The step's normals for the lane's P units: per noise block one Philox call
+// (counter (k, block, orbit, 0)) and Box-Muller.  A lane holding 1 or 2
+// units draws the block that contains them and transforms only the word pair
+// that holds them (several lanes of a group draw the same block).
+template <typename Real, int P>
+__device__ __forceinline__ void draw_normals(Real (&z)[P], uint32_t k, uint32_t orbit, int u0,
+                                             const PhiloxKeys &keys) {
+    if constexpr (P < 4) {
+        const U32x4 w = philox4x32_10(k, (uint32_t)(u0 >> 2), orbit, 0u, keys);
+        const bool high = (u0 & 2) != 0;
+        Real zz[2];
+        box_muller<Real>(high ? w.z : w.x, high ? w.w : w.y, zz[0], zz[1]);
+#pragma unroll
+        for (int i = 0; i < P; ++i) z[i] = (P == 1 && (u0 & 1)) ? zz[1] : zz[i];
+    } else {
+#pragma unroll
+        for (int blk = 0; blk < P / 4; ++blk) {
+            const U32x4 w = philox4x32_10(k, (uint32_t)(u0 >> 2) + (uint32_t)blk, orbit, 0u, keys);
+            box_muller<Real>(w.x, w.y, z[4 * blk], z[4 * blk + 1]);
+            box_muller<Real>(w.z, w.w, z[4 * blk + 2], z[4 * blk + 3]);
+        }
+    }
+}
+
+// One step of Eq. 2 for the lane's units: the normals (they do not depend on
+// the state, so they are drawn first and their latency overlaps the coupling
+// sums), the coupling sums over the orbit's lanes (RED), and the compensated
+// update of every unit.  Every unit's increment reads only the old state
+// (synchronous update).  With RECORD the normals are also written to zout
+// (the adjoint's replay).
+template <class M, typename Real, int P, bool RECORD = false, class RED>
 __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], uint32_t k,
-                                        uint32_t orbit, int u0, int units, const PhiloxKeys &keys,
+                                        uint32_t orbit, int u0, int units, const PhiloxKeys &keys, RED &reduce,
                                         Real (*zout)[P] = nullptr) {
+    static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
+    Real z[P];
+    if constexpr (M::kNoise) {
+        draw_normals<Real, P>(z, k, orbit, u0, keys);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) z[i] = Real(0);
+    }
     constexpr int NRA = M::NR > 0 ? M::NR : 1;
     Real red[NRA];
     model.prepare(x, cp, u0, units, red);
+    if constexpr (M::NR > 0) reduce(red);
 #pragma unroll
-    for (int r = 0; r < M::NR; ++r) red[r] = group_sum<G>(red[r]);
-    constexpr int NB = (P + 3) / 4;
+    for (int i = 0; i < P; ++i) {
+        Real inc[M::U];
+        model.incr(i, x, red, z[i], inc);
 #pragma unroll
-    for (int blk = 0; blk < NB; ++blk) {
-        Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-        if (M::kNoise) {
-            uint32_t b = (uint32_t)(u0 >> 2) + (uint32_t)blk;
-            U32x4 w = philox4x32_10(k, b, orbit, 0u, keys);
-            box_muller<Real>(w.x, w.y, z[0], z[1]);
-            if (P - 4 * blk > 2) box_muller<Real>(w.z, w.w, z[2], z[3]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = 4 * blk + q;
-            if (i < P) {
-                Real inc[M::U];
-                model.incr(i, x, red, z[q], inc);
-#pragma unroll
-                for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
-                if constexpr (RECORD) (*zout)[i] = z[q];
-            }
-        }
+        for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
+        if constexpr (RECORD) (*zout)[i] = z[i];
     }
 }
 
@@ -105,7 +164,7 @@ template <class M, typename Real, int G, int P>
 __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const ForwardArgs a) {
     constexpr int U = M::U;
     constexpr bool kKahan = std::is_same<Real, float>::value;
-    static_assert(G == 1 || P % 4 == 0, "multi-lane orbits need whole noise blocks per lane");
+    static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t orbit = tid / G;
     const int lig = (int)(tid & (G - 1));
@@ -137,8 +196,9 @@ __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const Forward
     uint32_t to_frame = a.stride - (a.k_begin % a.stride);
     uint32_t to_ckpt = a.ckpt_every ? a.ckpt_every - (a.k_begin % a.ckpt_every) : 0u;
 
+    WarpGroupSum<G> reduce;
     for (uint32_t k = a.k_begin; k < a.k_end; ++k) {
-        em_step<M, Real, G, P>(model, x, cp, k, gorb, u0, units, a.keys);
+        em_step<M, Real, P>(model, x, cp, k, gorb, u0, units, a.keys, reduce);
         if (frames != nullptr && --to_frame == 0) {
             to_frame = a.stride;
             const int64_t f = (int64_t)((k + 1) / a.stride);

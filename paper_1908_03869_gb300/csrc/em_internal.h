@@ -77,6 +77,70 @@ cudaError_t launch_adjoint(const AdjointArgs &a, Layout l, bool fp64, cudaStream
 cudaError_t launch_sum_over_orbits(const void *in, int64_t orbits, int32_t d, bool fp64, void *out,
                                    cudaStream_t s);
 
+// ---- Batched heterogeneous instances ------------------------------------
+// Every problem of a batch is an "instance" with its own n, steps, dt,
+// stride, orbits and buffers (concatenated); an "item" is one orbit of one
+// instance.  The persistent kernel's blocks (four warps) pull tasks from a
+// queue sorted longest-first: one item on all 128 lanes of the block, two
+// items on 64 lanes each (sums exchanged through shared memory), or four
+// warp tasks -- each up to 32/G items of one lane-group layout with similar
+// step counts.  Lanes hold at most 4 units, fewer for long items, so the
+// longest sequential chains are spread over more lanes.
+struct BatchInstance {
+    int32_t n, units, d;
+    int32_t param_stride;          // d, or 0 when the instance shares one parameter vector
+    uint32_t steps, stride, orbit_offset, has_frames;
+    int64_t orbits;
+    int64_t x_off, p_off, f_off;   // element offsets into the concatenated buffers
+    int64_t o_off;                 // offset of the instance's first orbit among all items (flags)
+    double dt;
+};
+
+struct BatchItem {
+    int32_t instance;
+    int32_t orbit;                 // orbit within the instance
+};
+
+struct BatchWarpTask {
+    int16_t layout;                // index into kBatchWarpLayoutG / P
+    int16_t count;                 // items in the task (<= 32 / G); 0 = idle warp
+    int32_t first;                 // first item index
+    uint32_t kmax;                 // largest step count among the task's items
+};
+
+enum : int32_t { kBatchWarps = 0, kBatchTeam128 = 1, kBatchTeam64 = 2 };
+
+struct BatchTask {
+    int32_t kind;                  // kBatchWarps, kBatchTeam128 or kBatchTeam64
+    int32_t team_p;                // units per lane of team items (1, 2 or 4)
+    int32_t item[2];               // team items (item[1] < 0: none)
+    BatchWarpTask warp[4];
+};
+
+constexpr int kBatchBlock = 128;   // threads per block of the batch kernel
+constexpr int kBatchNumWarpLayouts = 14;
+// Warp-task layouts, by index: (G lanes per item, P units per lane).
+constexpr int kBatchWarpLayoutG[kBatchNumWarpLayouts] = {1, 1, 1, 2, 4, 8, 16, 32, 2, 4, 8, 16, 32, 32};
+constexpr int kBatchWarpLayoutP[kBatchNumWarpLayouts] = {1, 2, 4, 4, 4, 4, 4, 4, 2, 2, 2, 2, 2, 1};
+
+struct BatchArgs {
+    const BatchInstance *inst;
+    const BatchItem *items;
+    const BatchTask *tasks;
+    int32_t ntasks;
+    int *head;                     // queue position, zeroed before each launch
+    const void *params;
+    void *x;
+    float *comp;
+    void *frames;                  // nullptr: no frames (tuning runs)
+    uint8_t *flags;
+    PhiloxKeys keys;
+};
+
+cudaError_t launch_batch(const BatchArgs &a, int grid, bool fp64, cudaStream_t s);
+// Blocks of the batch kernel resident per SM (occupancy of its launch bounds).
+int batch_blocks_per_sm(bool fp64);
+
 // Default layout for a number of units (smallest lane group holding them).
 inline bool default_layout(int units, Layout &l) {
     if (units <= 1) l = {1, 1};

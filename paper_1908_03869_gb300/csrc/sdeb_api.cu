@@ -5,8 +5,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "em_internal.h"
 #include "sdeb.h"
@@ -34,6 +36,24 @@ struct sdeb_ctx {
     bool params_set = false;
     int64_t k_current = 0;
     std::string err;
+    // ---- batch contexts (sdeb_create_batch) ----
+    bool is_batch = false;
+    std::vector<sdeb_problem> probs;
+    std::vector<BatchInstance> inst;      // host copy of the instance table
+    int64_t batch_params_bytes = 0, batch_state_elems = 0, batch_frame_elems = 0, batch_items = 0;
+    std::vector<Layout> inst_layout;
+    double batch_chain_frac = 0.5;        // longest chain allowed, as a fraction of the work per sub-partition
+    int num_sms = 1;
+    BatchInstance *d_inst = nullptr;
+    BatchItem *d_items = nullptr;
+    BatchTask *d_tasks = nullptr;
+    int *d_head = nullptr;
+    int32_t ntasks = 0, team_items = 0;
+    int grid = 0;
+    int grid_cap = 1;                     // resident blocks of the batch kernel on this device
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool batch_done = false;
 };
 
 namespace {
@@ -91,6 +111,18 @@ void free_buffers(sdeb_ctx *c) {
     cudaFree(c->d_seg);
     cudaFree(c->d_gradp);
     c->d_seg = c->d_gradp = nullptr;
+    cudaFree(c->d_inst);
+    cudaFree(c->d_items);
+    cudaFree(c->d_tasks);
+    cudaFree(c->d_head);
+    c->d_inst = nullptr;
+    c->d_items = nullptr;
+    c->d_tasks = nullptr;
+    c->d_head = nullptr;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    c->graph = nullptr;
+    c->capture_stream = nullptr;
     c->d_params = c->d_x = c->d_frames = c->d_ckpt = nullptr;
     c->d_comp = c->d_ckpt_comp = nullptr;
     c->d_flags = nullptr;
@@ -144,6 +176,276 @@ cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream
     const bool phase = a.model == kKuramoto || a.model == kKuramotoPaper;
     if (phase) return fp64 ? launch_forward_kuramoto_f64(a, l, s) : launch_forward_kuramoto_f32(a, l, s);
     return fp64 ? launch_forward_other_f64(a, l, s) : launch_forward_other_f32(a, l, s);
+}
+
+// ---- batch planning ---------------------------------------------------------
+
+// Warp-instructions per lane per step for a lane holding P units.
+double batch_step_cost(int P) { return P * 50.0 + 20.0; }
+
+int warp_layout_index(int G, int P) {
+    for (int l = 0; l < kBatchNumWarpLayouts; ++l)
+        if (kBatchWarpLayoutG[l] == G && kBatchWarpLayoutP[l] == P) return l;
+    return -1;
+}
+
+int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Lane count and units per lane of an item: the most units per lane (least
+// total work) whose sequential chain steps x cost(P) stays within chain_max,
+// else the fewest units per lane that exist.
+void choose_item_layout(int units, uint32_t steps, double chain_max, int &lanes, int &P) {
+    lanes = 0;
+    P = 0;
+    for (int p : {4, 2, 1}) {
+        const int l = pow2_at_least((units + p - 1) / p);
+        const bool ok = (l <= 32 && warp_layout_index(l, p) >= 0) || l == 64 || l == 128;
+        if (!ok) continue;
+        lanes = l;
+        P = p;
+        if ((double)steps * batch_step_cost(p) <= chain_max) return;
+    }
+}
+
+struct BatchPlan {
+    std::vector<BatchItem> items;
+    std::vector<BatchTask> tasks;
+    std::vector<Layout> inst_layout;   // (lanes per item, units per lane) of every instance
+    int32_t team_items = 0;
+};
+
+BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, int num_sms) {
+    double total_warp_instr = 0.0;
+    for (const BatchInstance &b : inst)
+        total_warp_instr += (double)b.steps * b.orbits * b.units * 50.0 / 32.0;
+    const double chain_max = chain_frac * total_warp_instr / (4.0 * std::max(1, num_sms));
+    struct Cand {
+        int32_t instance, orbit;
+        uint32_t steps;
+    };
+    std::vector<std::vector<Cand>> warp_items(kBatchNumWarpLayouts);
+    std::vector<Cand> team64[5], team128[5];   // by units per lane
+    BatchPlan plan;
+    plan.inst_layout.resize(inst.size());
+    for (int32_t i = 0; i < (int32_t)inst.size(); ++i) {
+        int lanes, P;
+        choose_item_layout(inst[i].units, inst[i].steps, chain_max, lanes, P);
+        plan.inst_layout[(size_t)i] = {lanes, P};
+        for (int64_t o = 0; o < inst[i].orbits; ++o) {
+            const Cand c{i, (int32_t)o, inst[i].steps};
+            if (lanes == 128) team128[P].push_back(c);
+            else if (lanes == 64) team64[P].push_back(c);
+            else warp_items[warp_layout_index(lanes, P)].push_back(c);
+        }
+    }
+    struct Costed {
+        BatchTask task;
+        double cost;
+    };
+    std::vector<Costed> tasks;
+    auto by_steps = [](const Cand &a, const Cand &b) { return a.steps > b.steps; };
+    for (int P : {1, 2, 4}) {
+        for (const Cand &c : team128[P]) {
+            BatchTask t{};
+            t.kind = kBatchTeam128;
+            t.team_p = P;
+            t.item[0] = (int32_t)plan.items.size();
+            t.item[1] = -1;
+            plan.items.push_back({c.instance, c.orbit});
+            tasks.push_back({t, (double)c.steps * batch_step_cost(P)});
+            ++plan.team_items;
+        }
+        std::vector<Cand> &v = team64[P];
+        std::stable_sort(v.begin(), v.end(), by_steps);
+        for (size_t q = 0; q < v.size(); q += 2) {
+            BatchTask t{};
+            t.kind = kBatchTeam64;
+            t.team_p = P;
+            t.item[0] = (int32_t)plan.items.size();
+            plan.items.push_back({v[q].instance, v[q].orbit});
+            t.item[1] = -1;
+            if (q + 1 < v.size()) {
+                t.item[1] = (int32_t)plan.items.size();
+                plan.items.push_back({v[q + 1].instance, v[q + 1].orbit});
+            }
+            tasks.push_back({t, (double)v[q].steps * batch_step_cost(P)});
+            plan.team_items += t.item[1] >= 0 ? 2 : 1;
+        }
+    }
+    struct CostedWarp {
+        BatchWarpTask wt;
+        double cost;
+    };
+    std::vector<CostedWarp> warps;
+    for (int l = 0; l < kBatchNumWarpLayouts; ++l) {
+        std::vector<Cand> &v = warp_items[l];
+        std::stable_sort(v.begin(), v.end(), by_steps);
+        const int cap = 32 / kBatchWarpLayoutG[l];
+        for (size_t b = 0; b < v.size(); b += cap) {
+            BatchWarpTask wt{};
+            wt.layout = (int16_t)l;
+            wt.first = (int32_t)plan.items.size();
+            wt.count = (int16_t)std::min<size_t>(cap, v.size() - b);
+            wt.kmax = 0;
+            for (int q = 0; q < wt.count; ++q) {
+                plan.items.push_back({v[b + q].instance, v[b + q].orbit});
+                wt.kmax = std::max(wt.kmax, v[b + q].steps);
+            }
+            warps.push_back({wt, (double)wt.kmax * batch_step_cost(kBatchWarpLayoutP[l])});
+        }
+    }
+    std::stable_sort(warps.begin(), warps.end(), [](const CostedWarp &a, const CostedWarp &b) { return a.cost > b.cost; });
+    for (size_t w = 0; w < warps.size(); w += 4) {
+        BatchTask t{};
+        t.kind = kBatchWarps;
+        t.item[0] = t.item[1] = -1;
+        double cost = 0.0;
+        for (size_t q = 0; q < 4 && w + q < warps.size(); ++q) {
+            t.warp[q] = warps[w + q].wt;
+            cost = std::max(cost, warps[w + q].cost);
+        }
+        tasks.push_back({t, cost});
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [](const Costed &a, const Costed &b) { return a.cost > b.cost; });
+    for (const Costed &c : tasks) plan.tasks.push_back(c.task);
+    return plan;
+}
+
+// Upload a plan into the context's tables (sized for the largest plan).
+sdeb_status upload_plan(sdeb_ctx *c, const BatchPlan &plan) {
+    cudaFree(c->d_items);
+    cudaFree(c->d_tasks);
+    c->d_items = nullptr;
+    c->d_tasks = nullptr;
+    cudaError_t e = cudaMalloc((void **)&c->d_items, sizeof(BatchItem) * std::max<size_t>(1, plan.items.size()));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_tasks, sizeof(BatchTask) * std::max<size_t>(1, plan.tasks.size()));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_items, plan.items.data(), sizeof(BatchItem) * plan.items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_tasks, plan.tasks.data(), sizeof(BatchTask) * plan.tasks.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(c, e, "batch plan upload");
+    }
+    c->ntasks = (int32_t)plan.tasks.size();
+    c->team_items = plan.team_items;
+    c->inst_layout = plan.inst_layout;
+    c->grid = std::max(1, std::min<int>(c->ntasks, c->grid_cap));
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return SDEB_OK;
+}
+
+BatchArgs batch_args(const sdeb_ctx *c, void *x, float *comp, void *frames, uint8_t *flags) {
+    BatchArgs a{};
+    a.inst = c->d_inst;
+    a.items = c->d_items;
+    a.tasks = c->d_tasks;
+    a.ntasks = c->ntasks;
+    a.head = c->d_head;
+    a.params = c->d_params;
+    a.x = x;
+    a.comp = comp;
+    a.frames = frames;
+    a.flags = flags;
+    a.keys = philox_key_schedule(c->pb.seed);
+    return a;
+}
+
+sdeb_status integrate_batch(sdeb_ctx *c, cudaStream_t s) {
+    if (!c->params_set) return fail(c, SDEB_ESTATE, "sdeb_set_params has not been called");
+    if (c->batch_done) return fail(c, SDEB_ESTATE, "batch already integrated; call sdeb_set_params to rerun");
+    cudaError_t e = cudaSuccess;
+    if (c->graph == nullptr) {
+        // one graph: reset the queue head, run the persistent kernel
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaMemsetAsync(c->d_head, 0, sizeof(int), c->capture_stream);
+            if (e1 == cudaSuccess)
+                e1 = launch_batch(batch_args(c, c->d_x, c->d_comp, c->d_frames, c->d_flags), c->grid,
+                                  c->pb.precision == SDEB_FP64, c->capture_stream);
+            e = cudaStreamEndCapture(c->capture_stream, &g);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->graph = nullptr;
+            return cuda_fail(c, e, "batch graph capture");
+        }
+    }
+    e = cudaGraphLaunch(c->graph, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(c, e, "batch graph launch");
+    }
+    c->batch_done = true;
+    c->k_current = c->pb.steps;
+    return SDEB_OK;
+}
+
+// Times the whole batch for each candidate plan (chain budget as a fraction
+// of the average work per SM sub-partition) on private copies of the state,
+// without frames, and keeps the fastest.
+sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
+    if (!c->params_set || c->batch_done)
+        return fail(c, SDEB_ESTATE, "call sdeb_autotune after sdeb_set_params and before integrating");
+    const bool fp64 = c->pb.precision == SDEB_FP64;
+    const size_t sb = (size_t)c->batch_state_elems * c->elem;
+    void *tx = nullptr;
+    float *tc = nullptr;
+    uint8_t *tf = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&tx, sb);
+    if (e == cudaSuccess && !fp64) e = cudaMalloc((void **)&tc, (size_t)c->batch_state_elems * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&tf, (size_t)c->batch_items);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best_frac = c->batch_chain_frac;
+    float best_ms = 1e30f;
+    bool first = true;
+    for (double frac : {0.125, 0.25, 0.5, 1.0, 4.0}) {
+        if (e != cudaSuccess) break;
+        if (upload_plan(c, plan_batch(c->inst, frac, c->num_sms)) != SDEB_OK) {
+            e = cudaErrorUnknown;
+            break;
+        }
+        float ms = 0.0f;
+        for (int rep = 0; rep < (first ? 2 : 1) && e == cudaSuccess; ++rep) {
+            e = cudaMemcpyAsync(tx, c->d_x, sb, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess && tc) e = cudaMemsetAsync(tc, 0, (size_t)c->batch_state_elems * 4, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_head, 0, sizeof(int), s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch_batch(batch_args(c, tx, tc, nullptr, tf), c->grid, fp64, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        first = false;
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best_frac = frac;
+        }
+    }
+    cudaFree(tx);
+    cudaFree(tc);
+    cudaFree(tf);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(c, e, "batch autotune");
+    }
+    c->batch_chain_frac = best_frac;
+    return upload_plan(c, plan_batch(c->inst, best_frac, c->num_sms));
 }
 
 }  // namespace
@@ -255,6 +557,23 @@ sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0, i
     if (!params || !x0) return fail(ctx, SDEB_EINVAL, "params and x0 must not be NULL");
     const cudaStream_t s = as_stream(stream);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (ctx->is_batch) {
+        const size_t sb = (size_t)ctx->batch_state_elems * ctx->elem;
+        cudaError_t e = cudaMemcpyAsync(ctx->d_params, params, (size_t)ctx->batch_params_bytes, kind, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_x, x0, sb, kind, s);
+        if (e == cudaSuccess && ctx->d_comp) e = cudaMemsetAsync(ctx->d_comp, 0, (size_t)ctx->batch_state_elems * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flags, 0, (size_t)ctx->batch_items, s);
+        if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->params_set = false;
+            return cuda_fail(ctx, e, "sdeb_set_params copy");
+        }
+        ctx->params_set = true;
+        ctx->batch_done = false;
+        ctx->k_current = 0;
+        return SDEB_OK;
+    }
     const size_t state_bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
     cudaError_t e = cudaMemcpyAsync(ctx->d_params, params, ctx->params_bytes, kind, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_x, x0, state_bytes, kind, s);
@@ -278,6 +597,7 @@ sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0, i
 
 sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "a batch integrates whole horizons (sdeb_integrate)");
     if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
     if (k_begin != ctx->k_current)
         return fail(ctx, SDEB_ESTATE, "k_begin=%lld but the state is at step %lld", (long long)k_begin,
@@ -317,6 +637,7 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
 
 sdeb_status sdeb_integrate(sdeb_ctx *ctx, void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return integrate_batch(ctx, as_stream(stream));
     if (ctx->params_set && ctx->k_current != 0)
         return fail(ctx, SDEB_ESTATE, "state is at step %lld; call sdeb_set_params to restart",
                     (long long)ctx->k_current);
@@ -326,6 +647,7 @@ sdeb_status sdeb_integrate(sdeb_ctx *ctx, void *stream) {
 sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int64_t frame_begin,
                              int64_t frame_count, int32_t dst_on_device, void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "use sdeb_batch_read on a batch");
     if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
     if (!ctx->d_frames) return fail(ctx, SDEB_ESTATE, "context was created without frames");
     if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
@@ -352,6 +674,7 @@ sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int64_t
 
 sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t dst_on_device, void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "use sdeb_batch_read on a batch");
     if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
     if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
     const size_t bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
@@ -383,6 +706,7 @@ sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream) {
 
 sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int32_t units_per_lane) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "a batch chooses layouts per instance (sdeb_autotune)");
     const int G = lanes_per_orbit, P = units_per_lane;
     if (!(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32) || P < 1 || P > 16 ||
         (G > 1 && P % 4 != 0) || (int64_t)G * P < ctx->units)
@@ -397,6 +721,7 @@ sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int32_t unit
 
 sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return autotune_batch(ctx, as_stream(stream));
     if (!ctx->params_set || ctx->k_current != 0)
         return fail(ctx, SDEB_ESTATE, "call sdeb_autotune after sdeb_set_params and before integrating");
     if (trial_steps <= 0) trial_steps = 64;
@@ -482,12 +807,16 @@ sdeb_status sdeb_get_layout(const sdeb_ctx *ctx, int32_t *lanes_per_orbit, int32
 sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *bytes) {
     if (!ctx || !ptr || !bytes) return fail(ctx, SDEB_EINVAL, "NULL argument");
     *ptr = ctx->d_frames;
-    *bytes = ctx->d_frames ? (size_t)ctx->nframes * ctx->pb.orbits * ctx->pb.n * ctx->elem : 0;
+    if (ctx->is_batch)
+        *bytes = ctx->d_frames ? (size_t)ctx->batch_frame_elems * ctx->elem : 0;
+    else
+        *bytes = ctx->d_frames ? (size_t)ctx->nframes * ctx->pb.orbits * ctx->pb.n * ctx->elem : 0;
     return SDEB_OK;
 }
 
 sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_dx0, void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "the adjoint is not available on batches");
     if (!dL_dxK || !dL_dp) return fail(ctx, SDEB_EINVAL, "dL_dxK and dL_dp must not be NULL");
     if (ctx->pb.model != SDEB_KURAMOTO && ctx->pb.model != SDEB_KURAMOTO_PAPER)
         return fail(ctx, SDEB_EUNSUPPORTED, "the adjoint is implemented for the Kuramoto models");
@@ -522,6 +851,156 @@ sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_d
         return fail(ctx, SDEB_EUNSUPPORTED, "no adjoint kernel for layout G=%d P=%d", ctx->layout.G, ctx->layout.P);
     if (e == cudaSuccess && shared) e = launch_sum_over_orbits(ctx->d_gradp, ctx->pb.orbits, ctx->pb.d, fp64, dL_dp, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_create_batch(const sdeb_problem *pbs, int32_t count, sdeb_ctx **out) {
+    if (!out) return fail(nullptr, SDEB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!pbs || count <= 0) return fail(nullptr, SDEB_EINVAL, "pbs must hold count >= 1 problems");
+    std::vector<BatchInstance> inst((size_t)count);
+    int64_t p_off = 0, x_off = 0, f_off = 0, o_off = 0;
+    int32_t max_n = 0;
+    int64_t max_steps = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const sdeb_problem &pb = pbs[i];
+        int32_t units = 0;
+        sdeb_status st = validate(&pb, units);
+        if (st != SDEB_OK) return fail(nullptr, st, "instance %d: %s", i, g_last_error.c_str());
+        if (pb.model != SDEB_KURAMOTO)
+            return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: batches run the SDEB_KURAMOTO model", i);
+        if (pb.precision != pbs[0].precision || pb.seed != pbs[0].seed)
+            return fail(nullptr, SDEB_EINVAL, "instance %d: precision and seed must match instance 0", i);
+        if (pb.ckpt_every != 0) return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: no checkpoints in a batch", i);
+        if (pb.orbits > 0x7fffffffLL) return fail(nullptr, SDEB_EINVAL, "instance %d: too many orbits", i);
+        const bool shared = pb.flags & SDEB_FLAG_SHARED_PARAMS;
+        const bool frames = !(pb.flags & SDEB_FLAG_NO_FRAMES);
+        BatchInstance &b = inst[(size_t)i];
+        b.n = pb.n;
+        b.units = units;
+        b.d = pb.d;
+        b.param_stride = shared ? 0 : pb.d;
+        b.steps = (uint32_t)pb.steps;
+        b.stride = (uint32_t)pb.stride;
+        b.orbit_offset = (uint32_t)pb.orbit_offset;
+        b.has_frames = frames ? 1u : 0u;
+        b.orbits = pb.orbits;
+        b.x_off = x_off;
+        b.p_off = p_off;
+        b.f_off = f_off;
+        b.o_off = o_off;
+        b.dt = pb.dt;
+        p_off += (shared ? 1 : pb.orbits) * pb.d;
+        x_off += pb.orbits * pb.n;
+        if (frames) f_off += (pb.steps / pb.stride + 1) * pb.orbits * pb.n;
+        o_off += pb.orbits;
+        max_n = std::max(max_n, pb.n);
+        max_steps = std::max<int64_t>(max_steps, pb.steps);
+    }
+    sdeb_ctx *c = new (std::nothrow) sdeb_ctx;
+    if (!c) return fail(nullptr, SDEB_ENOMEM, "host allocation failed");
+    c->is_batch = true;
+    c->probs.assign(pbs, pbs + count);
+    c->inst = inst;
+    c->pb = pbs[0];
+    c->pb.n = max_n;
+    c->pb.steps = max_steps;
+    c->pb.orbits = o_off;
+    c->elem = pbs[0].precision == SDEB_FP64 ? 8 : 4;
+    c->batch_params_bytes = p_off * (int64_t)c->elem;
+    c->batch_state_elems = x_off;
+    c->batch_frame_elems = f_off;
+    c->batch_items = o_off;
+    cudaError_t e = cudaGetDevice(&c->device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_params, (size_t)c->batch_params_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_x, (size_t)x_off * c->elem);
+    if (e == cudaSuccess && c->elem == 4) e = cudaMalloc((void **)&c->d_comp, (size_t)x_off * 4);
+    if (e == cudaSuccess && f_off > 0) e = cudaMalloc(&c->d_frames, (size_t)f_off * c->elem);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_flags, (size_t)o_off);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_inst, sizeof(BatchInstance) * inst.size());
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_head, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_inst, inst.data(), sizeof(BatchInstance) * inst.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sdeb_status st = cuda_fail(nullptr, e, "sdeb_create_batch");
+        free_buffers(c);
+        delete c;
+        return st;
+    }
+    c->num_sms = sms > 0 ? sms : 1;
+    c->grid_cap = c->num_sms * batch_blocks_per_sm(c->elem == 8);
+    sdeb_status st = upload_plan(c, plan_batch(c->inst, c->batch_chain_frac, c->num_sms));
+    if (st != SDEB_OK) {
+        free_buffers(c);
+        delete c;
+        return fail(nullptr, st, "batch plan upload failed");
+    }
+    *out = c;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_batch_read(sdeb_ctx *ctx, int32_t instance, int32_t what, void *dst, size_t dst_bytes,
+                            int32_t dst_on_device, void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (!ctx->is_batch) return fail(ctx, SDEB_EINVAL, "not a batch context");
+    if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
+    if (instance < 0 || instance >= (int32_t)ctx->inst.size())
+        return fail(ctx, SDEB_EINVAL, "instance %d outside [0, %d)", instance, (int)ctx->inst.size());
+    if (!ctx->batch_done) return fail(ctx, SDEB_ESTATE, "integrate the batch first");
+    const BatchInstance &b = ctx->inst[(size_t)instance];
+    const void *src = nullptr;
+    size_t bytes = 0;
+    if (what == 0) {
+        if (!b.has_frames) return fail(ctx, SDEB_ESTATE, "instance %d has no frames", instance);
+        bytes = (size_t)((b.steps / b.stride + 1) * b.orbits * b.n) * ctx->elem;
+        src = static_cast<const char *>(ctx->d_frames) + (size_t)b.f_off * ctx->elem;
+    } else if (what == 1) {
+        bytes = (size_t)(b.orbits * b.n) * ctx->elem;
+        src = static_cast<const char *>(ctx->d_x) + (size_t)b.x_off * ctx->elem;
+    } else {
+        return fail(ctx, SDEB_EINVAL, "what must be 0 (frames) or 1 (final state)");
+    }
+    if (dst_bytes != bytes) return fail(ctx, SDEB_EINVAL, "dst_bytes=%zu, expected %zu", dst_bytes, bytes);
+    const cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sdeb_batch_read copy");
+    }
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_batch_info(const sdeb_ctx *ctx, int32_t *tasks, int32_t *team_items, int32_t *grid) {
+    if (!ctx || !ctx->is_batch || !tasks || !team_items || !grid)
+        return fail(nullptr, SDEB_EINVAL, "batch context and outputs required");
+    *tasks = ctx->ntasks;
+    *team_items = ctx->team_items;
+    *grid = ctx->grid;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_batch_set_schedule(sdeb_ctx *ctx, double chain_fraction) {
+    if (!ctx || !ctx->is_batch) return fail(nullptr, SDEB_EINVAL, "batch context required");
+    if (!(chain_fraction > 0.0) || !std::isfinite(chain_fraction))
+        return fail(ctx, SDEB_EINVAL, "chain_fraction must be positive and finite");
+    if (ctx->params_set && ctx->batch_done)
+        return fail(ctx, SDEB_ESTATE, "set the schedule before integrating (after sdeb_set_params)");
+    ctx->batch_chain_frac = chain_fraction;
+    return upload_plan(ctx, plan_batch(ctx->inst, chain_fraction, ctx->num_sms));
+}
+
+sdeb_status sdeb_batch_layout(const sdeb_ctx *ctx, int32_t instance, int32_t *lanes, int32_t *units_per_lane) {
+    if (!ctx || !ctx->is_batch || !lanes || !units_per_lane)
+        return fail(nullptr, SDEB_EINVAL, "batch context and outputs required");
+    if (instance < 0 || instance >= (int32_t)ctx->inst_layout.size())
+        return fail(nullptr, SDEB_EINVAL, "instance %d out of range", instance);
+    *lanes = ctx->inst_layout[(size_t)instance].G;
+    *units_per_lane = ctx->inst_layout[(size_t)instance].P;
     return SDEB_OK;
 }
 

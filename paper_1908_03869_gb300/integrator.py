@@ -109,3 +109,82 @@ class Integrator:
         dx0 = torch.empty((pb.orbits, pb.n), dtype=self.dtype, device=dL_dxK.device) if want_dx0 else None
         sdeb_grad(self.ctx, _ptr(dL_dxK), _ptr(dp), _ptr(dx0) if dx0 is not None else None, self._stream(stream))
         return dp, dx0
+
+
+class BatchIntegrator:
+    """Owns one batch context (sdeb_create_batch): heterogeneous Kuramoto
+    instances integrated by one persistent, graph-launched kernel."""
+
+    def __init__(self, problems):
+        from . import sdeb_create_batch
+        self.pbs = list(problems)
+        self.dtype = torch.float64 if self.pbs[0].precision == SDEB_FP64 else torch.float32
+        self.ctx = sdeb_create_batch(self.pbs)
+
+    def close(self):
+        if self.ctx is not None:
+            sdeb_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream):
+        if stream is None:
+            return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        return getattr(stream, "cuda_stream", stream)
+
+    def set_params(self, params_list, x0_list, stream=None, device="cuda"):
+        """params_list[i]: [orbits_i][d_i] (or [d_i] if shared); x0_list[i]: [orbits_i][n_i]."""
+        p = torch.cat([torch.as_tensor(q, dtype=self.dtype).reshape(-1) for q in params_list]).to(device)
+        x = torch.cat([torch.as_tensor(q, dtype=self.dtype).reshape(-1) for q in x0_list]).to(device)
+        self._keep = (p, x)
+        sdeb_set_params(self.ctx, _ptr(p), _ptr(x), p.is_cuda, self._stream(stream))
+
+    def autotune(self, stream=None):
+        sdeb_autotune(self.ctx, 0, self._stream(stream))
+        return self.info()
+
+    def info(self):
+        from . import sdeb_batch_info
+        return sdeb_batch_info(self.ctx)
+
+    def set_schedule(self, chain_fraction):
+        from . import sdeb_batch_set_schedule
+        sdeb_batch_set_schedule(self.ctx, chain_fraction)
+
+    def layout(self, i):
+        from . import sdeb_batch_layout
+        return sdeb_batch_layout(self.ctx, i)
+
+    def integrate(self, stream=None):
+        sdeb_integrate(self.ctx, self._stream(stream))
+
+    def _read(self, i, what, shape, device, stream):
+        from . import sdeb_batch_read
+        out = torch.empty(shape, dtype=self.dtype, device=device)
+        sdeb_batch_read(self.ctx, i, what, _ptr(out), out.numel() * out.element_size(), out.is_cuda,
+                        self._stream(stream))
+        return out
+
+    def frames(self, i, device="cuda", stream=None):
+        pb = self.pbs[i]
+        return self._read(i, 0, (pb.steps // pb.stride + 1, pb.orbits, pb.n), device, stream)
+
+    def final(self, i, device="cuda", stream=None):
+        pb = self.pbs[i]
+        return self._read(i, 1, (pb.orbits, pb.n), device, stream)
+
+    def flags(self, stream=None):
+        out = torch.zeros(sum(pb.orbits for pb in self.pbs), dtype=torch.uint8)
+        sdeb_orbit_flags(self.ctx, _ptr(out), self._stream(stream))
+        return out
