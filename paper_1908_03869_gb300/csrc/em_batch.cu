@@ -84,20 +84,13 @@ __device__ __forceinline__ void run_warp_task(const BatchArgs &a, const BatchWar
 template <typename Real>
 __device__ __forceinline__ void run_warp_task_any(const BatchArgs &a, const BatchWarpTask &t) {
     switch (t.layout) {
-    case 0: run_warp_task<Real, 1, 1>(a, t); break;
-    case 1: run_warp_task<Real, 1, 2>(a, t); break;
-    case 2: run_warp_task<Real, 1, 4>(a, t); break;
-    case 3: run_warp_task<Real, 2, 4>(a, t); break;
-    case 4: run_warp_task<Real, 4, 4>(a, t); break;
-    case 5: run_warp_task<Real, 8, 4>(a, t); break;
-    case 6: run_warp_task<Real, 16, 4>(a, t); break;
-    case 7: run_warp_task<Real, 32, 4>(a, t); break;
-    case 8: run_warp_task<Real, 2, 2>(a, t); break;
-    case 9: run_warp_task<Real, 4, 2>(a, t); break;
-    case 10: run_warp_task<Real, 8, 2>(a, t); break;
-    case 11: run_warp_task<Real, 16, 2>(a, t); break;
-    case 12: run_warp_task<Real, 32, 2>(a, t); break;
-    case 13: run_warp_task<Real, 32, 1>(a, t); break;
+    case 0: run_warp_task<Real, 1, 4>(a, t); break;
+    case 1: run_warp_task<Real, 2, 4>(a, t); break;
+    case 2: run_warp_task<Real, 4, 4>(a, t); break;
+    case 3: run_warp_task<Real, 8, 4>(a, t); break;
+    case 4: run_warp_task<Real, 16, 4>(a, t); break;
+    case 5: run_warp_task<Real, 32, 4>(a, t); break;
+    case 6: run_warp_task<Real, 32, 2>(a, t); break;
     default: break;
     }
 }
@@ -159,20 +152,16 @@ __global__ void __launch_bounds__(kBatchBlock, 6) em_batch_kernel(const BatchArg
             const BatchWarpTask wt = task.warp[warp];
             if (wt.count > 0) run_warp_task_any<Real>(a, wt);
         } else if (task.kind == kBatchTeam128) {
-            if (task.team_p == 1) run_team<Real, 4, 1, 0>(a, task.item[0], s_red[0], 0);
-            else if (task.team_p == 2) run_team<Real, 4, 2, 0>(a, task.item[0], s_red[0], 0);
-            else run_team<Real, 4, 4, 0>(a, task.item[0], s_red[0], 0);
+            run_team<Real, 4, 2, 0>(a, task.item[0], s_red[0], 0);
         } else {
             const int half = warp >> 1;
             const int32_t item = task.item[half];
             if (item >= 0) {
                 if (half == 0) {
-                    if (task.team_p == 1) run_team<Real, 2, 1, 1>(a, item, s_red[0], 0);
-                    else if (task.team_p == 2) run_team<Real, 2, 2, 1>(a, item, s_red[0], 0);
+                    if (task.team_p == 2) run_team<Real, 2, 2, 1>(a, item, s_red[0], 0);
                     else run_team<Real, 2, 4, 1>(a, item, s_red[0], 0);
                 } else {
-                    if (task.team_p == 1) run_team<Real, 2, 1, 2>(a, item, s_red[1], 2);
-                    else if (task.team_p == 2) run_team<Real, 2, 2, 2>(a, item, s_red[1], 2);
+                    if (task.team_p == 2) run_team<Real, 2, 2, 2>(a, item, s_red[1], 2);
                     else run_team<Real, 2, 4, 2>(a, item, s_red[1], 2);
                 }
             }

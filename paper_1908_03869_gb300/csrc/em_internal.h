@@ -118,10 +118,13 @@ struct BatchTask {
 };
 
 constexpr int kBatchBlock = 128;   // threads per block of the batch kernel
-constexpr int kBatchNumWarpLayouts = 14;
-// Warp-task layouts, by index: (G lanes per item, P units per lane).
-constexpr int kBatchWarpLayoutG[kBatchNumWarpLayouts] = {1, 1, 1, 2, 4, 8, 16, 32, 2, 4, 8, 16, 32, 32};
-constexpr int kBatchWarpLayoutP[kBatchNumWarpLayouts] = {1, 2, 4, 4, 4, 4, 4, 4, 2, 2, 2, 2, 2, 1};
+constexpr int kBatchNumWarpLayouts = 7;
+// Warp-task layouts, by index: (G lanes per item, P units per lane).  Few
+// variants on purpose: every variant is a full inlined copy of the step,
+// and warps of one SM running many different variants thrash the
+// instruction cache.
+constexpr int kBatchWarpLayoutG[kBatchNumWarpLayouts] = {1, 2, 4, 8, 16, 32, 32};
+constexpr int kBatchWarpLayoutP[kBatchNumWarpLayouts] = {4, 4, 4, 4, 4, 4, 2};
 
 struct BatchArgs {
     const BatchInstance *inst;

@@ -197,13 +197,15 @@ int pow2_at_least(int v) {
 
 // Lane count and units per lane of an item: the most units per lane (least
 // total work) whose sequential chain steps x cost(P) stays within chain_max,
-// else the fewest units per lane that exist.
+// else the fewest units per lane that exist.  Layouts: 4 units per lane on
+// 1..32 lanes or a 64-lane team; 2 units per lane on 32 lanes or 64- and
+// 128-lane teams.
 void choose_item_layout(int units, uint32_t steps, double chain_max, int &lanes, int &P) {
     lanes = 0;
     P = 0;
-    for (int p : {4, 2, 1}) {
+    for (int p : {4, 2}) {
         const int l = pow2_at_least((units + p - 1) / p);
-        const bool ok = (l <= 32 && warp_layout_index(l, p) >= 0) || l == 64 || l == 128;
+        const bool ok = (l <= 32 && warp_layout_index(l, p) >= 0) || l == 64 || (l == 128 && p == 2);
         if (!ok) continue;
         lanes = l;
         P = p;
@@ -228,7 +230,7 @@ BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, 
         uint32_t steps;
     };
     std::vector<std::vector<Cand>> warp_items(kBatchNumWarpLayouts);
-    std::vector<Cand> team64[5], team128[5];   // by units per lane
+    std::vector<Cand> team64[5], team128[5];   // by units per lane (2 or 4)
     BatchPlan plan;
     plan.inst_layout.resize(inst.size());
     for (int32_t i = 0; i < (int32_t)inst.size(); ++i) {
@@ -248,7 +250,7 @@ BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, 
     };
     std::vector<Costed> tasks;
     auto by_steps = [](const Cand &a, const Cand &b) { return a.steps > b.steps; };
-    for (int P : {1, 2, 4}) {
+    for (int P : {2, 4}) {
         for (const Cand &c : team128[P]) {
             BatchTask t{};
             t.kind = kBatchTeam128;
@@ -392,9 +394,10 @@ sdeb_status integrate_batch(sdeb_ctx *c, cudaStream_t s) {
     return SDEB_OK;
 }
 
-// Times the whole batch for each candidate plan (chain budget as a fraction
-// of the average work per SM sub-partition) on private copies of the state,
-// without frames, and keeps the fastest.
+// Times the whole batch for each candidate plan -- chain budget (a fraction
+// of the average work per SM sub-partition) x resident blocks per SM (fewer
+// resident warps leave the long chains more issue slots) -- on private
+// copies of the state, without frames, and keeps the fastest.
 sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
     if (!c->params_set || c->batch_done)
         return fail(c, SDEB_ESTATE, "call sdeb_autotune after sdeb_set_params and before integrating");
@@ -410,10 +413,14 @@ sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best_frac = c->batch_chain_frac;
+    int best_grid = c->grid_cap;
     float best_ms = 1e30f;
     bool first = true;
-    for (double frac : {0.125, 0.25, 0.5, 1.0, 4.0}) {
+    const int cap = c->grid_cap;
+    for (double frac : {0.125, 0.25, 0.5, 2.0})
+      for (int per_sm : {2, 3, 4, 6}) {
         if (e != cudaSuccess) break;
+        c->grid_cap = std::min(cap, per_sm * c->num_sms);
         if (upload_plan(c, plan_batch(c->inst, frac, c->num_sms)) != SDEB_OK) {
             e = cudaErrorUnknown;
             break;
@@ -433,8 +440,10 @@ sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
         if (e == cudaSuccess && ms < best_ms) {
             best_ms = ms;
             best_frac = frac;
+            best_grid = c->grid_cap;
         }
-    }
+      }
+    c->grid_cap = best_grid;
     cudaFree(tx);
     cudaFree(tc);
     cudaFree(tf);
