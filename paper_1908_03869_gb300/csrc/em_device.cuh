@@ -94,41 +94,52 @@ __device__ __forceinline__ double uniform_f64(uint32_t w) {
 // Box-Muller, Eq. 3: n_cos = sqrt(-2 ln U1) cos(2 pi U2), n_sin = ... sin(...)
 // ---------------------------------------------------------------------------
 
+// SFU approximations in their flush-to-zero forms: every argument they get
+// here is a normal number or zero (uniforms >= 2^-33, radii of those, phases
+// reduced to [-pi, pi]), where the .ftz and plain forms return the same
+// value, and the .ftz forms skip the subnormal rescaling around the SFU.
 __device__ __forceinline__ float sqrt_approx_f32(float y) {
     float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(y));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
     return r;
 }
 
 __device__ __forceinline__ float lg2_approx_f32(float y) {
     float r;
-    asm("lg2.approx.f32 %0, %1;" : "=f"(r) : "f"(y));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
     return r;
+}
+
+__device__ __forceinline__ void sincos_approx_f32(float x, float &s, float &c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
 // FP32.  y = -2 ln U1 comes from the SFU log2 except when U1 is within 2^-6
 // of 1, where the absolute error of an SFU logarithm would dominate: there
 // t = 1 - U1 = (~w + 1/2) 2^-32 comes from the complement word and
-// -2 ln(1 - t) = 2 t (1 + t/2 + t^2/3 + t^3/4 + t^4/5) + O(t^6), the dropped
-// terms below 2^-26 relative for t <= 2^-6.  The angle uses the centred
-// uniform so the SFU sees an argument in [-pi, pi]:
-// cos(2 pi U2) = -cos(2 pi (U2 - 1/2)), likewise for sin.
+// -2 ln(1 - t) = t (2 + t + 2t^2/3 + t^3/2 + 2t^4/5) + O(t^6), the dropped
+// terms below 2^-26 relative for t <= 2^-6.  The angle is 2 pi (U2 - 1/2)
+// from the centred word in one rounding, an argument in [-pi, pi] for the
+// SFU: cos(2 pi U2) = -cos(2 pi (U2 - 1/2)), likewise for sin.
 __device__ __forceinline__ void box_muller_f32(uint32_t w_first, uint32_t w_second, float &n_cos,
                                                float &n_sin) {
     const float kMinus2Ln2 = -1.38629436111989061883f;  // -2 ln 2
     const uint32_t comp = ~w_first;                      // 2^32 - 1 - w
     const float t = uniform_f32(comp);                   // 1 - U1
-    float poly = __fmaf_rn(t, 0.2f, 0.25f);
-    poly = __fmaf_rn(poly, t, 1.0f / 3.0f);
-    poly = __fmaf_rn(poly, t, 0.5f);
+    float poly = __fmaf_rn(t, 0.4f, 0.5f);
+    poly = __fmaf_rn(poly, t, 2.0f / 3.0f);
     poly = __fmaf_rn(poly, t, 1.0f);
-    const float y_series = (2.0f * t) * poly;
+    poly = __fmaf_rn(poly, t, 2.0f);
+    const float y_series = t * poly;
     const float y_log = kMinus2Ln2 * lg2_approx_f32(uniform_f32(w_first));
     const float y = (comp < (1u << 26)) ? y_series : y_log;
     const float radius = sqrt_approx_f32(y);
-    const float ang = 6.28318530717958647692f * centered_uniform_f32(w_second);
+    // float(2 pi) 2^-32 and float(2 pi) 2^-33: exact scalings of float(2 pi)
+    const float ang = __fmaf_rn(__int2float_rn((int32_t)(w_second ^ 0x80000000u)), 0x1.921fb6p-30f,
+                                0x1.921fb6p-31f);
     float s, c;
-    __sincosf(ang, &s, &c);
+    sincos_approx_f32(ang, s, c);
     n_cos = -radius * c;
     n_sin = -radius * s;
 }
@@ -178,7 +189,7 @@ __device__ __forceinline__ float reduce_phase(float x, float c_comp) {
 // FP64 keeps the phase unreduced; sin/cos are CUDA's double functions.
 __device__ __forceinline__ double reduce_phase(double x, double c_comp) { return x - c_comp; }
 
-__device__ __forceinline__ void sincos_reduced(float r, float &s, float &c) { __sincosf(r, &s, &c); }
+__device__ __forceinline__ void sincos_reduced(float r, float &s, float &c) { sincos_approx_f32(r, s, c); }
 __device__ __forceinline__ void sincos_reduced(double r, double &s, double &c) { sincos(r, &s, &c); }
 
 __device__ __forceinline__ void sincos_phase(float x, float c_comp, float &s, float &c) {

@@ -29,46 +29,47 @@ struct KuramotoLane {
     static constexpr int U = 1;
     static constexpr int NR = 2;
     static constexpr bool kNoise = true;
-    Real omega[P];
+    Real omega_dt[P];         // omega_i dt
+    Real live[P];             // 1 for the orbit's units, 0 for padding
     Real gsq[PAPER ? P : 1];  // noise strength times sqrt(dt)
     Real kn;                  // K / n
-    Real dt;
+    Real kn_dt;               // (K / n) dt
     Real sn[P], cs[P];
 
-    __device__ __forceinline__ void load(const Real *p, int u0, int units, Real dt_, Real sqdt) {
-        dt = dt_;
+    __device__ __forceinline__ void load(const Real *p, int u0, int units, Real dt, Real sqdt) {
         kn = p[0] / (Real)units;
+        kn_dt = mul_r(kn, dt);
         if (!PAPER) gsq[0] = p[1] * sqdt;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             int j = u0 + i;
             bool ok = j < units;
-            omega[i] = ok ? p[(PAPER ? 1 : 2) + j] : Real(0);
+            omega_dt[i] = ok ? mul_r(p[(PAPER ? 1 : 2) + j], dt) : Real(0);
+            live[i] = ok ? Real(1) : Real(0);
             if (PAPER) gsq[i] = ok ? p[1 + units + j] * sqdt : Real(0);
         }
     }
 
-    __device__ __forceinline__ void prepare(const Real (&x)[U][P], const Real (&cp)[U][P], int u0, int units,
+    // Padding units enter the sums with weight 0: fma(1, v, s) == s + v.
+    __device__ __forceinline__ void prepare(const Real (&x)[U][P], const Real (&cp)[U][P], int, int,
                                             Real (&red)[NR]) {
         Real C = 0, S = 0;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             sincos_phase(x[0][i], cp[0][i], sn[i], cs[i]);
-            if (u0 + i < units) {
-                C += cs[i];
-                S += sn[i];
-            }
+            C = fma_r(live[i], cs[i], C);
+            S = fma_r(live[i], sn[i], S);
         }
         red[0] = C;
         red[1] = S;
     }
 
+    // f dt + g sqrt(dt) N = (K/n) dt (S cos - C sin) + (omega dt + g sqrt(dt) N)
     __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&red)[NR], Real N,
                                          Real (&inc)[U]) const {
         (void)x;
         const Real coupling = fma_r(red[1], cs[i], -mul_r(red[0], sn[i]));  // S cos - C sin
-        const Real f = fma_r(kn, coupling, omega[i]);
-        inc[0] = fma_r(f, dt, mul_r(gsq[PAPER ? i : 0], N));
+        inc[0] = fma_r(kn_dt, coupling, fma_r(gsq[PAPER ? i : 0], N, omega_dt[i]));
     }
 };
 
