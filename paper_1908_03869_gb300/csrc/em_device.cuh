@@ -125,15 +125,17 @@ __device__ __forceinline__ void sincos_approx_f32(float x, float &s, float &c) {
 __device__ __forceinline__ void box_muller_f32(uint32_t w_first, uint32_t w_second, float &n_cos,
                                                float &n_sin) {
     const float kMinus2Ln2 = -1.38629436111989061883f;  // -2 ln 2
-    const uint32_t comp = ~w_first;                      // 2^32 - 1 - w
-    const float t = uniform_f32(comp);                   // 1 - U1
+    // For w >= 2^31 the signed reading of w is w - 2^32 = -(comp + 1), comp =
+    // 2^32 - 1 - w the complement word, so t = 1 - U1 = (comp + 1/2) 2^-32 is
+    // one fma of it; t is only used when comp < 2^26.
+    const float t = __fmaf_rn(__int2float_rn((int32_t)w_first), -0x1p-32f, -0x1p-33f);
     float poly = __fmaf_rn(t, 0.4f, 0.5f);
     poly = __fmaf_rn(poly, t, 2.0f / 3.0f);
     poly = __fmaf_rn(poly, t, 1.0f);
     poly = __fmaf_rn(poly, t, 2.0f);
     const float y_series = t * poly;
     const float y_log = kMinus2Ln2 * lg2_approx_f32(uniform_f32(w_first));
-    const float y = (comp < (1u << 26)) ? y_series : y_log;
+    const float y = (w_first > 0xFBFFFFFFu) ? y_series : y_log;  // comp < 2^26
     const float radius = sqrt_approx_f32(y);
     // float(2 pi) 2^-32 and float(2 pi) 2^-33: exact scalings of float(2 pi)
     const float ang = __fmaf_rn(__int2float_rn((int32_t)(w_second ^ 0x80000000u)), 0x1.921fb6p-30f,

@@ -197,16 +197,28 @@ __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const Forward
     uint32_t to_ckpt = a.ckpt_every ? a.ckpt_every - (a.k_begin % a.ckpt_every) : 0u;
 
     WarpGroupSum<G> reduce;
-    for (uint32_t k = a.k_begin; k < a.k_end; ++k) {
-        em_step<M, Real, P>(model, x, cp, k, gorb, u0, units, a.keys, reduce);
-        if (frames != nullptr && --to_frame == 0) {
+    // Steps run in runs that end at the next frame, checkpoint or k_end, so
+    // the step loop itself carries no per-step bookkeeping.  FP32 unrolls two
+    // steps (more independent work between the SFU waits); FP64 keeps one,
+    // its registers are already near the limit.
+    constexpr int kRunUnroll = kKahan ? 2 : 1;
+    uint32_t k = a.k_begin;
+    while (k < a.k_end) {
+        uint64_t k_stop = a.k_end;
+        if (frames != nullptr) k_stop = min(k_stop, (uint64_t)k + to_frame);
+        if (ckpt != nullptr) k_stop = min(k_stop, (uint64_t)k + to_ckpt);
+        const uint32_t run = (uint32_t)(k_stop - k);
+#pragma unroll kRunUnroll
+        for (uint32_t s = 0; s < run; ++s) em_step<M, Real, P>(model, x, cp, k + s, gorb, u0, units, a.keys, reduce);
+        k += run;
+        if (frames != nullptr && (to_frame -= run) == 0) {
             to_frame = a.stride;
-            const int64_t f = (int64_t)((k + 1) / a.stride);
+            const int64_t f = (int64_t)(k / a.stride);
             if (active) store_units<Real, U, P>(frames + (f * a.orbits + o) * n, units, u0, x);
         }
-        if (ckpt != nullptr && --to_ckpt == 0) {
+        if (ckpt != nullptr && (to_ckpt -= run) == 0) {
             to_ckpt = a.ckpt_every;
-            const int64_t c = (int64_t)((k + 1) / a.ckpt_every);
+            const int64_t c = (int64_t)(k / a.ckpt_every);
             if (active) {
                 store_units<Real, U, P>(ckpt + (c * a.orbits + o) * n, units, u0, x);
                 if constexpr (kKahan)
