@@ -145,22 +145,24 @@ SDEB_API sdeb_status sdeb_create_batch(const sdeb_problem *pbs, int32_t count, s
 SDEB_API sdeb_status sdeb_batch_read(sdeb_ctx *ctx, int32_t instance, int32_t what, void *dst, size_t dst_bytes,
                                      int32_t dst_on_device, void *stream);
 
-/* Schedule of a batch: queue tasks, items run as two-warp teams, and the
- * persistent grid size (blocks of 64 threads). */
+/* Schedule of a batch: queue tasks, items run as multi-warp teams (64 or
+ * 128 lanes), and the persistent grid size (blocks of 128 threads). */
 SDEB_API sdeb_status sdeb_batch_info(const sdeb_ctx *ctx, int32_t *tasks, int32_t *team_items, int32_t *grid);
 
 /* Schedule knob of a batch (sdeb_autotune picks it by timing): each orbit
- * gets the most units per lane (at most 4) whose sequential chain, steps x
- * per-step cost, stays within chain_fraction x the batch's average work per
- * SM sub-partition; fewer units per lane spread a long orbit over more lanes
- * (up to a 128-lane team).  Results depend on the schedule only through the
- * order of the coupling sums.  EINVAL unless chain_fraction > 0. */
+ * takes the layout of least total work -- 8 or 4 units per lane in a packed
+ * warp, or a 64-lane (4 or 2 units per lane) or 128-lane (2) team --
+ * among those whose sequential chain, steps x per-step cost, stays within
+ * chain_fraction x the batch's average work per SM sub-partition, else the
+ * layout with the shortest chain.  Packed warps hold several orbits side
+ * by side of similar step counts.  An orbit's results depend on the
+ * schedule only through its own layout (the order of its coupling sums).
+ * EINVAL unless chain_fraction > 0. */
 SDEB_API sdeb_status sdeb_batch_set_schedule(sdeb_ctx *ctx, double chain_fraction);
 
-/* Lane layout the current schedule gives the orbits of `instance`: lanes
- * per orbit (1..32 within a warp, 64 or 128 for a multi-warp team) and
- * units per lane.  The orbit's trajectory equals that of a single-problem
- * context with the same layout (sdeb_set_layout) when lanes <= 32. */
+/* Layout the current schedule gives the orbits of `instance`: lanes per
+ * orbit (ceil(n / units_per_lane) <= 32 in a packed warp, 64 or 128 for a
+ * multi-warp team) and units per lane (8, 4 or 2). */
 SDEB_API sdeb_status sdeb_batch_layout(const sdeb_ctx *ctx, int32_t instance, int32_t *lanes, int32_t *units_per_lane);
 
 /* Free the context and its device buffers (synchronises the device first).

@@ -4,11 +4,12 @@
 // instances with the longest sequential chains start at once.  Work sizing
 // replaces the hand-tuned work-group sizes of the paper's Table 4.
 //
-// Each item (one orbit of one instance) runs Eq. 2 with exactly the step
-// code of the forward kernel (em_step), so an item integrated in a warp task
-// with layout (G, P) is bit-identical to the same orbit in a single-problem
-// context using that layout.  No block ever waits on another: the only
-// shared state is the queue head, advanced with atomicAdd.
+// Each item (one orbit of one instance) runs Eq. 2 with the step code of the
+// forward kernel (em_step); its coupling sums run over its own lanes only,
+// in an order fixed by its layout, so an item's results do not depend on
+// the other items or on the schedule beyond its (lanes, units per lane).
+// No block ever waits on another: the only shared state is the queue head,
+// advanced with atomicAdd.
 #include "em_forward_impl.cuh"
 
 namespace sdeb {
@@ -72,27 +73,59 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
     }
 }
 
-template <typename Real, int G, int P>
-__device__ __forceinline__ void run_warp_task(const BatchArgs &a, const BatchWarpTask &t) {
-    const int lane = threadIdx.x & 31;
-    const int g = lane / G;
-    const bool has = g < t.count;
-    WarpGroupSum<G> reduce;
-    run_item<Real, P>(a, a.items[t.first + (has ? g : 0)], has, lane % G, t.kmax, reduce);
-}
-
-template <typename Real>
-__device__ __forceinline__ void run_warp_task_any(const BatchArgs &a, const BatchWarpTask &t) {
-    switch (t.layout) {
-    case 0: run_warp_task<Real, 1, 4>(a, t); break;
-    case 1: run_warp_task<Real, 2, 4>(a, t); break;
-    case 2: run_warp_task<Real, 4, 4>(a, t); break;
-    case 3: run_warp_task<Real, 8, 4>(a, t); break;
-    case 4: run_warp_task<Real, 16, 4>(a, t); break;
-    case 5: run_warp_task<Real, 32, 4>(a, t); break;
-    case 6: run_warp_task<Real, 32, 2>(a, t); break;
-    default: break;
+// Sums over one item's lanes [s, e) of a packed warp: an inclusive scan by
+// shfl_up -- at level q a lane adds the partial of the lane 2^q below while
+// that lane is in the segment, so after level q lane L holds the sum over
+// [max(L - 2^(q+1) + 1, s), L] -- then lane e - 1's total is broadcast.  The
+// addition tree depends only on L - s: an item's sums, and so its orbit,
+// are the same bits wherever it sits in the warp.  Levels past the warp's
+// longest segment add nothing and are skipped (the count is warp-uniform).
+struct SegmentSum {
+    int last;       // e - 1
+    int levels;     // ceil(log2(longest segment of the warp))
+    unsigned take;  // bit q: L - 2^q >= s
+    template <typename Real, int NR>
+    __device__ __forceinline__ void operator()(Real (&r)[NR]) const {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            if (q >= levels) break;
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const Real t = __shfl_up_sync(0xffffffffu, r[j], 1u << q);
+                if (take & (1u << q)) r[j] += t;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j) r[j] = __shfl_sync(0xffffffffu, r[j], last);
     }
+};
+
+// A packed warp: the task's items lie side by side in lane order, item j on
+// ceil(units_j / P) lanes.  Lanes past the last item idle through the steps
+// on a one-lane segment of their own (the scans need every lane).
+template <typename Real, int P>
+__device__ __forceinline__ void run_packed_warp(const BatchArgs &a, const BatchWarpTask &t) {
+    const int lane = threadIdx.x & 31;
+    int start = 0, mine = -1, s = lane, e = lane + 1, longest = 1;
+    for (int j = 0; j < t.count; ++j) {
+        const int len = (a.inst[a.items[t.first + j].instance].units + P - 1) / P;
+        if (lane >= start && lane < start + len) {
+            mine = j;
+            s = start;
+            e = start + len;
+        }
+        longest = max(longest, len);
+        start += len;
+    }
+    SegmentSum reduce;
+    reduce.last = e - 1;
+    reduce.levels = 32 - __clz(longest - 1);
+    reduce.take = 0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        if (lane - (1 << q) >= s) reduce.take |= 1u << q;
+    const bool has = mine >= 0;
+    run_item<Real, P>(a, a.items[t.first + (has ? mine : 0)], has, lane - s, t.kmax, reduce);
 }
 
 // Team of NW warps on one item; BAR = 0 is the whole block's barrier,
@@ -137,7 +170,7 @@ __device__ __forceinline__ void run_team(const BatchArgs &a, int32_t item, Real 
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kBatchBlock, 6) em_batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kBatchBlock, 4) em_batch_kernel(const BatchArgs a) {
     __shared__ int s_task;
     __shared__ Real s_red[2][2 * 4 * 2];
     for (;;) {
@@ -146,11 +179,15 @@ __global__ void __launch_bounds__(kBatchBlock, 6) em_batch_kernel(const BatchArg
         const int t = s_task;
         __syncthreads();
         if (t >= a.ntasks) return;
-        const BatchTask task = a.tasks[t];
+        const BatchTask &task = a.tasks[t];  // read in place: the warp index is not a constant
         const int warp = threadIdx.x >> 5;
         if (task.kind == kBatchWarps) {
             const BatchWarpTask wt = task.warp[warp];
-            if (wt.count > 0) run_warp_task_any<Real>(a, wt);
+            switch (wt.count > 0 ? wt.p : 0) {
+            case 8: run_packed_warp<Real, 8>(a, wt); break;
+            case 4: run_packed_warp<Real, 4>(a, wt); break;
+            default: break;
+            }
         } else if (task.kind == kBatchTeam128) {
             run_team<Real, 4, 2, 0>(a, task.item[0], s_red[0], 0);
         } else {

@@ -83,8 +83,10 @@ cudaError_t launch_sum_over_orbits(const void *in, int64_t orbits, int32_t d, bo
 // instance.  The persistent kernel's blocks (four warps) pull tasks from a
 // queue sorted longest-first: one item on all 128 lanes of the block, two
 // items on 64 lanes each (sums exchanged through shared memory), or four
-// warp tasks -- each up to 32/G items of one lane-group layout with similar
-// step counts.  Lanes hold at most 4 units, fewer for long items, so the
+// packed warps.  A packed warp holds several items side by side, each on
+// ceil(units / P) consecutive lanes (P = 8 or 4 units per lane), items of
+// similar step counts; an item's coupling sums are a segmented scan over
+// its own lanes.  Long items get fewer units per lane (teams), so the
 // longest sequential chains are spread over more lanes.
 struct BatchInstance {
     int32_t n, units, d;
@@ -102,29 +104,22 @@ struct BatchItem {
 };
 
 struct BatchWarpTask {
-    int16_t layout;                // index into kBatchWarpLayoutG / P
-    int16_t count;                 // items in the task (<= 32 / G); 0 = idle warp
+    int16_t p;                     // units per lane: 8 or 4
+    int16_t count;                 // items in the warp, in lane order; 0 = idle warp
     int32_t first;                 // first item index
-    uint32_t kmax;                 // largest step count among the task's items
+    uint32_t kmax;                 // largest step count among the warp's items
 };
 
 enum : int32_t { kBatchWarps = 0, kBatchTeam128 = 1, kBatchTeam64 = 2 };
 
 struct BatchTask {
     int32_t kind;                  // kBatchWarps, kBatchTeam128 or kBatchTeam64
-    int32_t team_p;                // units per lane of team items (1, 2 or 4)
+    int32_t team_p;                // units per lane of team items (2 or 4)
     int32_t item[2];               // team items (item[1] < 0: none)
     BatchWarpTask warp[4];
 };
 
 constexpr int kBatchBlock = 128;   // threads per block of the batch kernel
-constexpr int kBatchNumWarpLayouts = 7;
-// Warp-task layouts, by index: (G lanes per item, P units per lane).  Few
-// variants on purpose: every variant is a full inlined copy of the step,
-// and warps of one SM running many different variants thrash the
-// instruction cache.
-constexpr int kBatchWarpLayoutG[kBatchNumWarpLayouts] = {1, 2, 4, 8, 16, 32, 32};
-constexpr int kBatchWarpLayoutP[kBatchNumWarpLayouts] = {4, 4, 4, 4, 4, 4, 2};
 
 struct BatchArgs {
     const BatchInstance *inst;

@@ -180,37 +180,46 @@ cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream
 
 // ---- batch planning ---------------------------------------------------------
 
-// Warp-instructions per lane per step for a lane holding P units.
-double batch_step_cost(int P) { return P * 50.0 + 20.0; }
+// Thread-instructions per lane per step for a lane holding P units: the
+// phase, sums and update of every unit, the normals (a lane with fewer than
+// four units still draws a whole Philox block), the lane's share of the
+// coupling-sum exchange (segmented scan in a packed warp; butterfly plus
+// shared memory and a barrier in a team) and the loop.
+double batch_step_cost(int P, bool team) { return P * 28.0 + std::max(P, 4) / 4 * 38.0 + (team ? 43.0 : 30.0); }
 
-int warp_layout_index(int G, int P) {
-    for (int l = 0; l < kBatchNumWarpLayouts; ++l)
-        if (kBatchWarpLayoutG[l] == G && kBatchWarpLayoutP[l] == P) return l;
-    return -1;
-}
+// Where an item runs: a packed warp with P = 8 or 4 units per lane on
+// ceil(units / P) <= 32 lanes, or a team of 64 lanes (P = 4 or 2) or 128
+// lanes (P = 2).  An item takes the layout of least total work (lanes x
+// per-step cost) among those whose sequential chain, steps x per-step cost,
+// stays within chain_max, else the layout with the shortest chain.
+struct ItemLayout {
+    int lanes = 0, P = 0;
+    bool team = false;
+};
 
-int pow2_at_least(int v) {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
-
-// Lane count and units per lane of an item: the most units per lane (least
-// total work) whose sequential chain steps x cost(P) stays within chain_max,
-// else the fewest units per lane that exist.  Layouts: 4 units per lane on
-// 1..32 lanes or a 64-lane team; 2 units per lane on 32 lanes or 64- and
-// 128-lane teams.
-void choose_item_layout(int units, uint32_t steps, double chain_max, int &lanes, int &P) {
-    lanes = 0;
-    P = 0;
-    for (int p : {4, 2}) {
-        const int l = pow2_at_least((units + p - 1) / p);
-        const bool ok = (l <= 32 && warp_layout_index(l, p) >= 0) || l == 64 || (l == 128 && p == 2);
-        if (!ok) continue;
-        lanes = l;
-        P = p;
-        if ((double)steps * batch_step_cost(p) <= chain_max) return;
+ItemLayout choose_item_layout(int units, uint32_t steps, double chain_max) {
+    ItemLayout cand[7];
+    int nc = 0;
+    for (int P : {8, 4})
+        if ((units + P - 1) / P <= 32) cand[nc++] = {(units + P - 1) / P, P, false};
+    for (int P : {4, 2})
+        if (units <= 64 * P && units > 16 * P) cand[nc++] = {64, P, true};
+    if (units > 128 && units <= 256) cand[nc++] = {128, 2, true};
+    ItemLayout best, shortest;
+    double best_work = 0.0, shortest_chain = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        const double per_step = batch_step_cost(cand[c].P, cand[c].team);
+        const double chain = (double)steps * per_step, work = chain * cand[c].lanes;
+        if (chain <= chain_max && (best.P == 0 || work < best_work)) {
+            best = cand[c];
+            best_work = work;
+        }
+        if (shortest.P == 0 || chain < shortest_chain) {
+            shortest = cand[c];
+            shortest_chain = chain;
+        }
     }
+    return best.P != 0 ? best : shortest;
 }
 
 struct BatchPlan {
@@ -223,25 +232,25 @@ struct BatchPlan {
 BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, int num_sms) {
     double total_warp_instr = 0.0;
     for (const BatchInstance &b : inst)
-        total_warp_instr += (double)b.steps * b.orbits * b.units * 50.0 / 32.0;
+        total_warp_instr += (double)b.steps * b.orbits * b.units * batch_step_cost(8, false) / 8.0 / 32.0;
     const double chain_max = chain_frac * total_warp_instr / (4.0 * std::max(1, num_sms));
     struct Cand {
         int32_t instance, orbit;
         uint32_t steps;
+        int lanes;
     };
-    std::vector<std::vector<Cand>> warp_items(kBatchNumWarpLayouts);
+    std::vector<Cand> packed[9];               // by units per lane (8 or 4)
     std::vector<Cand> team64[5], team128[5];   // by units per lane (2 or 4)
     BatchPlan plan;
     plan.inst_layout.resize(inst.size());
     for (int32_t i = 0; i < (int32_t)inst.size(); ++i) {
-        int lanes, P;
-        choose_item_layout(inst[i].units, inst[i].steps, chain_max, lanes, P);
-        plan.inst_layout[(size_t)i] = {lanes, P};
+        const ItemLayout l = choose_item_layout(inst[i].units, inst[i].steps, chain_max);
+        plan.inst_layout[(size_t)i] = {l.lanes, l.P};
         for (int64_t o = 0; o < inst[i].orbits; ++o) {
-            const Cand c{i, (int32_t)o, inst[i].steps};
-            if (lanes == 128) team128[P].push_back(c);
-            else if (lanes == 64) team64[P].push_back(c);
-            else warp_items[warp_layout_index(lanes, P)].push_back(c);
+            const Cand c{i, (int32_t)o, inst[i].steps, l.lanes};
+            if (!l.team) packed[l.P].push_back(c);
+            else if (l.lanes == 128) team128[l.P].push_back(c);
+            else team64[l.P].push_back(c);
         }
     }
     struct Costed {
@@ -258,7 +267,7 @@ BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, 
             t.item[0] = (int32_t)plan.items.size();
             t.item[1] = -1;
             plan.items.push_back({c.instance, c.orbit});
-            tasks.push_back({t, (double)c.steps * batch_step_cost(P)});
+            tasks.push_back({t, (double)c.steps * batch_step_cost(P, true)});
             ++plan.team_items;
         }
         std::vector<Cand> &v = team64[P];
@@ -274,30 +283,52 @@ BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, 
                 t.item[1] = (int32_t)plan.items.size();
                 plan.items.push_back({v[q + 1].instance, v[q + 1].orbit});
             }
-            tasks.push_back({t, (double)v[q].steps * batch_step_cost(P)});
+            tasks.push_back({t, (double)v[q].steps * batch_step_cost(P, true)});
             plan.team_items += t.item[1] >= 0 ? 2 : 1;
         }
     }
+    // Packed warps: items sorted by steps are cut into buckets whose step
+    // counts lie within a factor kBucket (a warp steps until its longest
+    // item ends), and each bucket is packed first-fit by decreasing lanes.
+    const double kBucket = 1.2;
     struct CostedWarp {
         BatchWarpTask wt;
         double cost;
     };
     std::vector<CostedWarp> warps;
-    for (int l = 0; l < kBatchNumWarpLayouts; ++l) {
-        std::vector<Cand> &v = warp_items[l];
+    for (int P : {8, 4}) {
+        std::vector<Cand> &v = packed[P];
         std::stable_sort(v.begin(), v.end(), by_steps);
-        const int cap = 32 / kBatchWarpLayoutG[l];
-        for (size_t b = 0; b < v.size(); b += cap) {
-            BatchWarpTask wt{};
-            wt.layout = (int16_t)l;
-            wt.first = (int32_t)plan.items.size();
-            wt.count = (int16_t)std::min<size_t>(cap, v.size() - b);
-            wt.kmax = 0;
-            for (int q = 0; q < wt.count; ++q) {
-                plan.items.push_back({v[b + q].instance, v[b + q].orbit});
-                wt.kmax = std::max(wt.kmax, v[b + q].steps);
+        for (size_t b0 = 0; b0 < v.size();) {
+            size_t b1 = b0;
+            while (b1 < v.size() && (double)v[b1].steps * kBucket >= (double)v[b0].steps) ++b1;
+            std::vector<Cand> bucket(v.begin() + (std::ptrdiff_t)b0, v.begin() + (std::ptrdiff_t)b1);
+            std::stable_sort(bucket.begin(), bucket.end(), [](const Cand &a, const Cand &b) { return a.lanes > b.lanes; });
+            std::vector<std::vector<Cand>> bins;
+            std::vector<int> used;
+            for (const Cand &c : bucket) {
+                size_t w = 0;
+                while (w < bins.size() && used[w] + c.lanes > 32) ++w;
+                if (w == bins.size()) {
+                    bins.emplace_back();
+                    used.push_back(0);
+                }
+                bins[w].push_back(c);
+                used[w] += c.lanes;
             }
-            warps.push_back({wt, (double)wt.kmax * batch_step_cost(kBatchWarpLayoutP[l])});
+            for (const std::vector<Cand> &bin : bins) {
+                BatchWarpTask wt{};
+                wt.p = (int16_t)P;
+                wt.first = (int32_t)plan.items.size();
+                wt.count = (int16_t)bin.size();
+                wt.kmax = 0;
+                for (const Cand &c : bin) {
+                    plan.items.push_back({c.instance, c.orbit});
+                    wt.kmax = std::max(wt.kmax, c.steps);
+                }
+                warps.push_back({wt, (double)wt.kmax * batch_step_cost(P, false)});
+            }
+            b0 = b1;
         }
     }
     std::stable_sort(warps.begin(), warps.end(), [](const CostedWarp &a, const CostedWarp &b) { return a.cost > b.cost; });
@@ -417,8 +448,8 @@ sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
     float best_ms = 1e30f;
     bool first = true;
     const int cap = c->grid_cap;
-    for (double frac : {0.125, 0.25, 0.5, 2.0})
-      for (int per_sm : {2, 3, 4, 6}) {
+    for (double frac : {0.125, 0.25, 0.5, 1.0, 2.0})
+      for (int per_sm : {2, 3, 4}) {
         if (e != cudaSuccess) break;
         c->grid_cap = std::min(cap, per_sm * c->num_sms);
         if (upload_plan(c, plan_batch(c->inst, frac, c->num_sms)) != SDEB_OK) {
