@@ -48,7 +48,7 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one forward launch of the n = 32 problem, from
 # the ncu capture summarised in profiles/em_forward_kuramoto_fp32_n32_dram_full_size.md;
 # set to None whenever the forward kernel changes until it is measured again.
-FORWARD_N32_DRAM_BYTES = None
+FORWARD_N32_DRAM_BYTES = 3.52e9
 
 
 def _dist_env():
@@ -422,11 +422,12 @@ def _time_adjoint(stream, rank, reps=5):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     with Integrator(mk(0)) as plain, Integrator(mk(W["ckpt_every"])) as ck:
         # dL/dX^K of the mean order parameter at T, from the library's kernel
+        # each context tuned for what it runs: the plain forward alone, the
+        # checkpointed context for forward + adjoint
         for it in (plain, ck):
             it.set_params(pt, xt, stream=stream)
             it.autotune(trial_steps=64, stream=stream)
-        lay = plain.layout()
-        ck.set_layout(*lay)
+        lay, fwd_lay = ck.layout(), plain.layout()
         ck.integrate(stream=stream)
         xK = ck.final(stream=stream)
         r = torch.empty(orbits, dtype=torch.float32, device="cuda")
@@ -456,7 +457,7 @@ def _time_adjoint(stream, rank, reps=5):
     t_plain, t_fwd, t_adj = [statistics.median(t[1:]) for t in (t_plain, t_fwd, t_adj)]
     units = orbits * W["steps"]
     return {"workload": "kuramoto n=32, 16384 orbits, shared params, dt=0.01, 2000 steps, ckpt every 100, fp32",
-            "layout_G_P": list(lay),
+            "layout_G_P": list(lay), "fwd_layout_G_P": list(fwd_lay),
             "fwd_ms": t_plain, "fwd_ckpt_ms": t_fwd, "adjoint_ms": t_adj,
             "fwd_plus_adjoint_orbit_steps_per_sec": units / ((t_fwd + t_adj) / 1e3),
             "fwd_orbit_steps_per_sec": units / (t_plain / 1e3),

@@ -233,9 +233,14 @@ SDEB_API sdeb_status sdeb_get_layout(const sdeb_ctx *ctx, int32_t *lanes_per_orb
  * Table 4): times the forward kernel over the first trial_steps steps
  * (<= 0: 64) for every instantiated layout that covers the orbit's units
  * with at most 2x padding, on private copies of the current state, and keeps
- * the fastest.  Call after sdeb_set_params and before integrating (ESTATE
- * otherwise).  The context's state, frames and checkpoints are untouched.
- * Allocates and frees temporary device buffers; synchronises `stream`. */
+ * the fastest.  A context created with ckpt_every > 0 for sdeb_grad is tuned
+ * for forward + adjoint instead: both are timed over the first
+ * min(ckpt_every, 1024, steps) steps (trial_steps is ignored), the adjoint
+ * from checkpoint 0 with a zero dL/dX^K into temporary outputs.  Call after
+ * sdeb_set_params and before integrating (ESTATE otherwise).  The context's
+ * state, frames and checkpoints are untouched (the adjoint's segment scratch
+ * is overwritten).  Allocates and frees temporary device buffers;
+ * synchronises `stream`. */
 SDEB_API sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream);
 
 SDEB_API const char *sdeb_last_error(const sdeb_ctx *ctx);

@@ -89,12 +89,26 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             }
         }
         // ---- reverse sweep ---------------------------------------------------
+        // the next row (step k - 1) is loaded while step k is processed
+        Real rn[1][P], zn[1][P];
+        {
+            const Real *row = seg + ((int64_t)(k1 - 1 - k0) * a.orbits + o) * (2 * n);
+            load_units<Real, 1, P>(row, units, u0, rn);
+            load_units<Real, 1, P>(row + n, units, u0, zn);
+        }
         for (uint32_t kk = k1; kk > k0; --kk) {
             const uint32_t k = kk - 1;
             Real r[1][P], z[1][P];
-            const Real *row = seg + ((int64_t)(k - k0) * a.orbits + o) * (2 * n);
-            load_units<Real, 1, P>(row, units, u0, r);
-            load_units<Real, 1, P>(row + n, units, u0, z);
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                r[0][i] = rn[0][i];
+                z[0][i] = zn[0][i];
+            }
+            if (k > k0) {
+                const Real *row = seg + ((int64_t)(k - 1 - k0) * a.orbits + o) * (2 * n);
+                load_units<Real, 1, P>(row, units, u0, rn);
+                load_units<Real, 1, P>(row + n, units, u0, zn);
+            }
             Real sn[P], cs[P];
             Real C = 0, S = 0, A = 0, B = 0;
 #pragma unroll

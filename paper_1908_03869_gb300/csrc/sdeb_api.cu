@@ -764,7 +764,12 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
     if (ctx->is_batch) return autotune_batch(ctx, as_stream(stream));
     if (!ctx->params_set || ctx->k_current != 0)
         return fail(ctx, SDEB_ESTATE, "call sdeb_autotune after sdeb_set_params and before integrating");
+    // A context that keeps checkpoints for sdeb_grad is tuned for forward +
+    // adjoint: both are timed over one segment (at most 1024 steps) from
+    // checkpoint 0, which sdeb_set_params has written.
+    const bool tune_adjoint = ctx->d_seg != nullptr;
     if (trial_steps <= 0) trial_steps = 64;
+    if (tune_adjoint) trial_steps = std::min<int64_t>((int64_t)ctx->pb.ckpt_every, 1024);
     if (trial_steps > ctx->pb.steps) trial_steps = ctx->pb.steps;
     if (trial_steps == 0) return SDEB_OK;
     static const Layout kCandidates[] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 4}, {2, 8}, {4, 4}, {4, 8}, {4, 16},
@@ -774,10 +779,14 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
     void *tx = nullptr;
     float *tc = nullptr;
     uint8_t *tf = nullptr;
+    void *t_dl = nullptr, *t_dp = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaMalloc(&tx, state_bytes);
     if (e == cudaSuccess && ctx->d_comp) e = cudaMalloc((void **)&tc, (size_t)ctx->pb.orbits * ctx->pb.n * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&tf, (size_t)ctx->pb.orbits);
+    if (e == cudaSuccess && tune_adjoint) e = cudaMalloc(&t_dl, state_bytes);
+    if (e == cudaSuccess && tune_adjoint) e = cudaMemsetAsync(t_dl, 0, state_bytes, s);
+    if (e == cudaSuccess && tune_adjoint) e = cudaMalloc(&t_dp, (size_t)ctx->pb.orbits * ctx->pb.d * ctx->elem);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     Layout best = ctx->layout;
@@ -814,6 +823,35 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         }
+        if (e == cudaSuccess && tune_adjoint) {
+            AdjointArgs g{};
+            g.model = ctx->pb.model;
+            g.n = ctx->pb.n;
+            g.units = ctx->units;
+            g.d = ctx->pb.d;
+            g.orbits = ctx->pb.orbits;
+            g.params = ctx->d_params;
+            g.param_stride = a.param_stride;
+            g.ckpt = ctx->d_ckpt;
+            g.ckpt_comp = ctx->d_ckpt_comp;
+            g.ckpt_every = (uint32_t)ctx->pb.ckpt_every;
+            g.steps = (uint32_t)trial_steps;
+            g.orbit_offset = a.orbit_offset;
+            g.dt = ctx->pb.dt;
+            g.seg = ctx->d_seg;
+            g.dL_dxK = t_dl;
+            g.dL_dp = t_dp;
+            g.keys = a.keys;
+            float ms_adj = 0.0f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = launch_adjoint(g, l, ctx->pb.precision == SDEB_FP64, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_adj, e0, e1);
+            }
+            ms += ms_adj;
+        }
         if (e == cudaErrorNotSupported) {
             e = cudaSuccess;
             cudaGetLastError();
@@ -827,6 +865,8 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
     cudaFree(tx);
     cudaFree(tc);
     cudaFree(tf);
+    cudaFree(t_dl);
+    cudaFree(t_dp);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) {

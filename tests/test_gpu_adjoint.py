@@ -193,3 +193,37 @@ def test_order_param_kernel(precision):
         rr, rdr = oracle.order_param(th[o].astype(np.float64))
         assert abs(r[o] - rr) < tol
         assert np.abs(dr[o] - rdr).max() < tol * 10
+
+
+def test_autotune_on_a_checkpointed_context_keeps_the_gradient_consistent():
+    """sdeb_autotune on a context with checkpoints times forward + adjoint;
+    it leaves the checkpoints intact (checkpoint 0 is x0), and the gradient
+    after tuning equals the gradient of a fresh context set to the chosen
+    layout, bit for bit, and the FP64 oracle adjoint to 1e-3 (FP32)."""
+    import torch
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    n, orbits, dt, steps, ckpt, seed = 32, 512, 0.01, 250, 100, 3
+    p, x0 = inputs.kuramoto(n, orbits, seed=4)
+    p, x0 = p.astype(np.float32), x0.astype(np.float32)
+    rng = np.random.Generator(np.random.PCG64(8))
+    dL = rng.standard_normal((orbits, n)).astype(np.float32)
+    pb = sdeb.Problem.make("kuramoto", n, orbits, dt, steps, 1, seed, "fp32", ckpt_every=ckpt, no_frames=True)
+    res = []
+    for tuned in (True, False):
+        with Integrator(pb) as it:
+            it.set_params(torch.tensor(p).cuda(), torch.tensor(x0).cuda())
+            if tuned:
+                lay = it.autotune()
+            else:
+                it.set_layout(*lay)
+            it.integrate()
+            dp, dx0 = it.grad(torch.tensor(dL).cuda())
+            res.append((it.final().cpu().numpy(), dp.cpu().numpy(), dx0.cpu().numpy()))
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, b)
+    m, d = sdeb.model_shape("kuramoto", n)
+    opb = oracle.make_problem("kuramoto", n, m, d, dt, steps, 1, seed)
+    dp_o, dx0_o = oracle.adjoint(opb, p.astype(np.float64), x0.astype(np.float64), dL.astype(np.float64))
+    assert _rel(res[0][1], dp_o) < 1e-3
+    assert _rel(res[0][2], dx0_o) < 1e-3
