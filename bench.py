@@ -48,7 +48,8 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one forward launch of the n = 32 problem, from
 # the ncu capture summarised in profiles/em_forward_kuramoto_fp32_n32_dram_full_size.md;
 # set to None whenever the forward kernel changes until it is measured again.
-FORWARD_N32_DRAM_BYTES = 3.52e9
+FORWARD_N32_DRAM_BYTES = None
+E2E_CHUNKS = 4
 
 
 def _dist_env():
@@ -273,11 +274,29 @@ def run_ours(args):
         h2d = sum(p.numel() * p.element_size() + x.numel() * x.element_size() for p, x in host_inputs)
         d2h = sum(f.numel() * f.element_size() for f in host_frames)
 
+        # The horizon runs in E2E_CHUNKS ranges; each range's frames go to the
+        # host on a second stream while the next range (or problem) computes.
+        copy_stream = torch.cuda.Stream()
+        copied = [torch.cuda.Event() for _ in its]
+        for ev in copied:
+            ev.record(copy_stream)
+
         def e2e_step():
             for i, it in enumerate(its):
+                stream.wait_event(copied[i])      # the previous step's frames of this problem are out
                 it.set_params(*host_inputs[i], stream=stream)
-                it.integrate(stream=stream)
-                it.frames(out=host_frames[i], stream=stream)
+                f_done = 0
+                for c in range(E2E_CHUNKS):
+                    k0, k1 = c * STEPS // E2E_CHUNKS, (c + 1) * STEPS // E2E_CHUNKS
+                    it.integrate_range(k0, k1, stream=stream)
+                    ready = torch.cuda.Event()
+                    ready.record(stream)
+                    copy_stream.wait_event(ready)
+                    f_end = k1 // STRIDE + 1
+                    it.frames(begin=f_done, count=f_end - f_done, out=host_frames[i][f_done:f_end],
+                              stream=copy_stream)
+                    f_done = f_end
+                copied[i].record(copy_stream)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -289,7 +308,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         e2e = {"value": units_per_step * ws * args.steps / e2e_s, "unit": "orbit-steps/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "pipeline": "%d integrate_range chunks per problem; frames copied to pinned host memory on a "
+                           "second stream while the next chunk computes" % E2E_CHUNKS}
         del host_frames
 
     # ---- FP64 on a 1000-step prefix of the same problems -----------------
