@@ -54,17 +54,29 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
     Real *frames = a.frames != nullptr && in.has_frames ? static_cast<Real *>(a.frames) + in.f_off : nullptr;
     if (has && frames != nullptr) store_units<Real, 1, P>(frames + (int64_t)it.orbit * n, units, u0, x);
     const uint32_t gorb = in.orbit_offset + (uint32_t)it.orbit;
+    const uint32_t steps = in.steps;
     uint32_t to_frame = in.stride;
-    for (uint32_t k = 0; k < kmax; ++k) {
-        em_step<M, Real, P>(model, x, cp, k, gorb, u0, units, a.keys, reduce);
-        if (has && k < in.steps) {
-            if (--to_frame == 0) {
+    // Steps run in runs that end at the next event (a frame or the end) of
+    // any item of the warp, so the step loop carries no per-step checks; the
+    // run length is the warp's minimum, the same in every warp of a team.
+    uint32_t k = 0;
+    while (k < kmax) {
+        const bool live = has && k < steps;
+        uint32_t mine = kmax - k;
+        if (live) mine = min(mine, min(to_frame, steps - k));
+        const uint32_t run = __reduce_min_sync(0xffffffffu, mine);
+#pragma unroll 1
+        for (uint32_t s = 0; s < run; ++s) em_step<M, Real, P>(model, x, cp, k + s, gorb, u0, units, a.keys, reduce);
+        k += run;
+        if (live) {
+            to_frame -= run;
+            if (to_frame == 0) {
                 to_frame = in.stride;
-                const int64_t f = (int64_t)((k + 1) / in.stride);
                 if (frames != nullptr)
-                    store_units<Real, 1, P>(frames + (f * in.orbits + it.orbit) * n, units, u0, x);
+                    store_units<Real, 1, P>(frames + ((int64_t)(k / in.stride) * in.orbits + it.orbit) * n, units, u0,
+                                            x);
             }
-            if (k + 1 == in.steps) {
+            if (k == steps) {
                 store_units<Real, 1, P>(xrow, units, u0, x);
                 if constexpr (kKahan) store_units<float, 1, P>(crow, units, u0, cp);
                 flag_nonfinite<Real, P>(a.flags + in.o_off + it.orbit, x, u0, units);
