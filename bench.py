@@ -48,7 +48,7 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one forward launch of the n = 32 problem, from
 # the ncu capture summarised in profiles/em_forward_kuramoto_fp32_n32_dram_full_size.md;
 # set to None whenever the forward kernel changes until it is measured again.
-FORWARD_N32_DRAM_BYTES = None
+FORWARD_N32_DRAM_BYTES = 3.50e9
 E2E_CHUNKS = 4
 
 
