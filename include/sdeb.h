@@ -165,6 +165,24 @@ SDEB_API sdeb_status sdeb_batch_set_schedule(sdeb_ctx *ctx, double chain_fractio
  * multi-warp team) and units per lane (8, 4 or 2). */
 SDEB_API sdeb_status sdeb_batch_layout(const sdeb_ctx *ctx, int32_t instance, int32_t *lanes, int32_t *units_per_lane);
 
+/* Host-only view of the schedule sdeb_create_batch + sdeb_batch_set_schedule
+ * (chain_fraction) would build for pbs on a device with num_sms SMs; makes no
+ * CUDA call.  The problems are validated as by sdeb_create_batch.  Outputs,
+ * each optional (NULL to skip):
+ *   lanes, units_per_lane [count]: the layout of each instance's orbits, as
+ *     sdeb_batch_layout reports it;
+ *   item_task, item_slot, item_lane0 [total_orbits], one entry per orbit of
+ *     every instance in order: the queue position of the orbit's task, where
+ *     in the task it runs (0..3: packed warp w; 4, 5: first or second half of
+ *     a two-team task; 6: the whole block) and, in a packed warp, its first
+ *     lane (0 otherwise).  total_orbits must equal the sum of the instances'
+ *     orbits when any of the three is given (EINVAL otherwise);
+ *   ntasks: the number of queue tasks.
+ * EINVAL unless chain_fraction > 0 and num_sms >= 1. */
+SDEB_API sdeb_status sdeb_batch_plan(const sdeb_problem *pbs, int32_t count, double chain_fraction, int32_t num_sms,
+                                     int32_t *lanes, int32_t *units_per_lane, int64_t total_orbits,
+                                     int32_t *item_task, int32_t *item_slot, int32_t *item_lane0, int32_t *ntasks);
+
 /* Free the context and its device buffers (synchronises the device first).
  * NULL is accepted. */
 SDEB_API void sdeb_destroy(sdeb_ctx *ctx);

@@ -24,7 +24,8 @@ __all__ = [
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
     "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
-    "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "model_shape", "EXPORTED_SYMBOLS",
+    "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "sdeb_batch_plan", "model_shape",
+    "EXPORTED_SYMBOLS",
 ]
 
 SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
@@ -108,6 +109,8 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_int32)]),
     "sdeb_batch_set_schedule": (_ST, [_P, ctypes.c_double]),
     "sdeb_batch_layout": (_ST, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "sdeb_batch_plan": (_ST, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P,
+                              _P, ctypes.POINTER(ctypes.c_int32)]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -220,6 +223,25 @@ def sdeb_batch_info(ctx):
 
 def sdeb_batch_set_schedule(ctx, chain_fraction):
     _check(lib().sdeb_batch_set_schedule(ctx, float(chain_fraction)), ctx)
+
+
+def sdeb_batch_plan(problems, chain_fraction, num_sms):
+    """Host-only schedule of a batch (no GPU needed).  Returns a dict of numpy
+    arrays: lanes and units_per_lane per instance; task, slot and lane0 per
+    orbit of every instance in order; and the task count."""
+    import numpy as np
+    arr = (Problem * len(problems))(*problems) if not isinstance(problems, ctypes.Array) else problems
+    total = sum(int(p.orbits) for p in arr)
+    lanes = np.zeros(len(arr), np.int32)
+    upl = np.zeros(len(arr), np.int32)
+    task = np.full(total, -1, np.int32)
+    slot = np.full(total, -1, np.int32)
+    lane0 = np.full(total, -1, np.int32)
+    nt = ctypes.c_int32()
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(lib().sdeb_batch_plan(ctypes.cast(arr, _P), len(arr), float(chain_fraction), int(num_sms), ptr(lanes),
+                                 ptr(upl), total, ptr(task), ptr(slot), ptr(lane0), ctypes.byref(nt)))
+    return {"lanes": lanes, "units_per_lane": upl, "task": task, "slot": slot, "lane0": lane0, "tasks": nt.value}
 
 
 def sdeb_batch_layout(ctx, instance):

@@ -488,6 +488,59 @@ sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
     return upload_plan(c, plan_batch(c->inst, best_frac, c->num_sms));
 }
 
+// Validates the problems of a batch and lays out their instances in the
+// concatenated buffers (host only, no CUDA call).
+struct BatchLayoutSums {
+    int64_t p_off = 0, x_off = 0, f_off = 0, o_off = 0;
+    int32_t max_n = 0;
+    int64_t max_steps = 0;
+};
+
+sdeb_status build_batch_instances(const sdeb_problem *pbs, int32_t count, std::vector<BatchInstance> &inst,
+                                  BatchLayoutSums &sums) {
+    if (!pbs || count <= 0) return fail(nullptr, SDEB_EINVAL, "pbs must hold count >= 1 problems");
+    inst.assign((size_t)count, BatchInstance{});
+    int64_t &p_off = sums.p_off, &x_off = sums.x_off, &f_off = sums.f_off, &o_off = sums.o_off;
+    int32_t &max_n = sums.max_n;
+    int64_t &max_steps = sums.max_steps;
+    for (int32_t i = 0; i < count; ++i) {
+        const sdeb_problem &pb = pbs[i];
+        int32_t units = 0;
+        sdeb_status st = validate(&pb, units);
+        if (st != SDEB_OK) return fail(nullptr, st, "instance %d: %s", i, g_last_error.c_str());
+        if (pb.model != SDEB_KURAMOTO)
+            return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: batches run the SDEB_KURAMOTO model", i);
+        if (pb.precision != pbs[0].precision || pb.seed != pbs[0].seed)
+            return fail(nullptr, SDEB_EINVAL, "instance %d: precision and seed must match instance 0", i);
+        if (pb.ckpt_every != 0) return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: no checkpoints in a batch", i);
+        if (pb.orbits > 0x7fffffffLL) return fail(nullptr, SDEB_EINVAL, "instance %d: too many orbits", i);
+        const bool shared = pb.flags & SDEB_FLAG_SHARED_PARAMS;
+        const bool frames = !(pb.flags & SDEB_FLAG_NO_FRAMES);
+        BatchInstance &b = inst[(size_t)i];
+        b.n = pb.n;
+        b.units = units;
+        b.d = pb.d;
+        b.param_stride = shared ? 0 : pb.d;
+        b.steps = (uint32_t)pb.steps;
+        b.stride = (uint32_t)pb.stride;
+        b.orbit_offset = (uint32_t)pb.orbit_offset;
+        b.has_frames = frames ? 1u : 0u;
+        b.orbits = pb.orbits;
+        b.x_off = x_off;
+        b.p_off = p_off;
+        b.f_off = f_off;
+        b.o_off = o_off;
+        b.dt = pb.dt;
+        p_off += (shared ? 1 : pb.orbits) * pb.d;
+        x_off += pb.orbits * pb.n;
+        if (frames) f_off += (pb.steps / pb.stride + 1) * pb.orbits * pb.n;
+        o_off += pb.orbits;
+        max_n = std::max(max_n, pb.n);
+        max_steps = std::max<int64_t>(max_steps, pb.steps);
+    }
+    return SDEB_OK;
+}
+
 }  // namespace
 
 namespace sdeb {
@@ -937,46 +990,13 @@ sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_d
 sdeb_status sdeb_create_batch(const sdeb_problem *pbs, int32_t count, sdeb_ctx **out) {
     if (!out) return fail(nullptr, SDEB_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!pbs || count <= 0) return fail(nullptr, SDEB_EINVAL, "pbs must hold count >= 1 problems");
-    std::vector<BatchInstance> inst((size_t)count);
-    int64_t p_off = 0, x_off = 0, f_off = 0, o_off = 0;
-    int32_t max_n = 0;
-    int64_t max_steps = 0;
-    for (int32_t i = 0; i < count; ++i) {
-        const sdeb_problem &pb = pbs[i];
-        int32_t units = 0;
-        sdeb_status st = validate(&pb, units);
-        if (st != SDEB_OK) return fail(nullptr, st, "instance %d: %s", i, g_last_error.c_str());
-        if (pb.model != SDEB_KURAMOTO)
-            return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: batches run the SDEB_KURAMOTO model", i);
-        if (pb.precision != pbs[0].precision || pb.seed != pbs[0].seed)
-            return fail(nullptr, SDEB_EINVAL, "instance %d: precision and seed must match instance 0", i);
-        if (pb.ckpt_every != 0) return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: no checkpoints in a batch", i);
-        if (pb.orbits > 0x7fffffffLL) return fail(nullptr, SDEB_EINVAL, "instance %d: too many orbits", i);
-        const bool shared = pb.flags & SDEB_FLAG_SHARED_PARAMS;
-        const bool frames = !(pb.flags & SDEB_FLAG_NO_FRAMES);
-        BatchInstance &b = inst[(size_t)i];
-        b.n = pb.n;
-        b.units = units;
-        b.d = pb.d;
-        b.param_stride = shared ? 0 : pb.d;
-        b.steps = (uint32_t)pb.steps;
-        b.stride = (uint32_t)pb.stride;
-        b.orbit_offset = (uint32_t)pb.orbit_offset;
-        b.has_frames = frames ? 1u : 0u;
-        b.orbits = pb.orbits;
-        b.x_off = x_off;
-        b.p_off = p_off;
-        b.f_off = f_off;
-        b.o_off = o_off;
-        b.dt = pb.dt;
-        p_off += (shared ? 1 : pb.orbits) * pb.d;
-        x_off += pb.orbits * pb.n;
-        if (frames) f_off += (pb.steps / pb.stride + 1) * pb.orbits * pb.n;
-        o_off += pb.orbits;
-        max_n = std::max(max_n, pb.n);
-        max_steps = std::max<int64_t>(max_steps, pb.steps);
-    }
+    std::vector<BatchInstance> inst;
+    BatchLayoutSums sums;
+    sdeb_status st0 = build_batch_instances(pbs, count, inst, sums);
+    if (st0 != SDEB_OK) return st0;
+    const int64_t p_off = sums.p_off, x_off = sums.x_off, f_off = sums.f_off, o_off = sums.o_off;
+    const int32_t max_n = sums.max_n;
+    const int64_t max_steps = sums.max_steps;
     sdeb_ctx *c = new (std::nothrow) sdeb_ctx;
     if (!c) return fail(nullptr, SDEB_ENOMEM, "host allocation failed");
     c->is_batch = true;
@@ -1072,6 +1092,55 @@ sdeb_status sdeb_batch_set_schedule(sdeb_ctx *ctx, double chain_fraction) {
         return fail(ctx, SDEB_ESTATE, "set the schedule before integrating (after sdeb_set_params)");
     ctx->batch_chain_frac = chain_fraction;
     return upload_plan(ctx, plan_batch(ctx->inst, chain_fraction, ctx->num_sms));
+}
+
+sdeb_status sdeb_batch_plan(const sdeb_problem *pbs, int32_t count, double chain_fraction, int32_t num_sms,
+                            int32_t *lanes, int32_t *units_per_lane, int64_t total_orbits, int32_t *item_task,
+                            int32_t *item_slot, int32_t *item_lane0, int32_t *ntasks) {
+    if (!(chain_fraction > 0.0) || !std::isfinite(chain_fraction))
+        return fail(nullptr, SDEB_EINVAL, "chain_fraction must be positive and finite");
+    if (num_sms < 1) return fail(nullptr, SDEB_EINVAL, "num_sms must be >= 1");
+    std::vector<BatchInstance> inst;
+    BatchLayoutSums sums;
+    sdeb_status st = build_batch_instances(pbs, count, inst, sums);
+    if (st != SDEB_OK) return st;
+    const bool per_item = item_task || item_slot || item_lane0;
+    if (per_item && total_orbits != sums.o_off)
+        return fail(nullptr, SDEB_EINVAL, "total_orbits is %lld, the batch holds %lld orbits", (long long)total_orbits,
+                    (long long)sums.o_off);
+    const BatchPlan plan = plan_batch(inst, chain_fraction, num_sms);
+    for (int32_t i = 0; i < count; ++i) {
+        if (lanes) lanes[i] = plan.inst_layout[(size_t)i].G;
+        if (units_per_lane) units_per_lane[i] = plan.inst_layout[(size_t)i].P;
+    }
+    if (ntasks) *ntasks = (int32_t)plan.tasks.size();
+    if (!per_item) return SDEB_OK;
+    auto place = [&](int32_t item, int32_t t, int32_t slot, int32_t lane0) {
+        const BatchItem &it = plan.items[(size_t)item];
+        const int64_t g = inst[(size_t)it.instance].o_off + it.orbit;
+        if (item_task) item_task[g] = t;
+        if (item_slot) item_slot[g] = slot;
+        if (item_lane0) item_lane0[g] = lane0;
+    };
+    for (int32_t t = 0; t < (int32_t)plan.tasks.size(); ++t) {
+        const BatchTask &task = plan.tasks[(size_t)t];
+        if (task.kind == kBatchWarps) {
+            for (int w = 0; w < 4; ++w) {
+                const BatchWarpTask &wt = task.warp[w];
+                int32_t lane = 0;
+                for (int j = 0; j < wt.count; ++j) {
+                    place(wt.first + j, t, w, lane);
+                    lane += (inst[(size_t)plan.items[(size_t)(wt.first + j)].instance].units + wt.p - 1) / wt.p;
+                }
+            }
+        } else if (task.kind == kBatchTeam128) {
+            place(task.item[0], t, 6, 0);
+        } else {
+            for (int h = 0; h < 2; ++h)
+                if (task.item[h] >= 0) place(task.item[h], t, 4 + h, 0);
+        }
+    }
+    return SDEB_OK;
 }
 
 sdeb_status sdeb_batch_layout(const sdeb_ctx *ctx, int32_t instance, int32_t *lanes, int32_t *units_per_lane) {
