@@ -36,6 +36,7 @@ class Problem(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("shared_params", ctypes.c_int32),
         ("mean_field", ctypes.c_int32),
+        ("milstein", ctypes.c_int32),
     ]
 
 
@@ -63,6 +64,7 @@ def lib():
                                      ctypes.c_int32, _P]
         L.oracle_drift.argtypes = [ctypes.POINTER(Problem), ctypes.c_double, _P, _P, _P]
         L.oracle_diffusion.argtypes = [ctypes.POINTER(Problem), ctypes.c_double, _P, _P, _P]
+        L.oracle_diffusion_diag_derivative.argtypes = [ctypes.POINTER(Problem), ctypes.c_double, _P, _P, _P]
         L.oracle_check_problem.argtypes = [ctypes.POINTER(Problem)]
         L.oracle_integrate.argtypes = [ctypes.POINTER(Problem), _P, _P, ctypes.c_int64,
                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P,
@@ -79,10 +81,10 @@ def _ptr(a):
 
 
 def make_problem(model, n, m, d, dt, steps, stride=1, seed=0, t0=0.0,
-                 shared_params=False, mean_field=False):
+                 shared_params=False, mean_field=False, milstein=False):
     return Problem(MODELS[model] if isinstance(model, str) else int(model), n, m, d, float(t0),
                    float(dt), int(steps), int(stride), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                   int(bool(shared_params)), int(bool(mean_field)))
+                   int(bool(shared_params)), int(bool(mean_field)), int(bool(milstein)))
 
 
 def philox(ctr, key):
@@ -129,6 +131,15 @@ def diffusion(pb, x, p, t=0.0):
     g = np.zeros((pb.n, max(pb.m, 1)), dtype=np.float64)
     assert lib().oracle_diffusion(ctypes.byref(pb), t, _ptr(x), _ptr(p), _ptr(g)) == 0
     return g[:, :pb.m]
+
+
+def diffusion_diag_derivative(pb, x, p, t=0.0):
+    """d g_jj / d x_j for j < m (diagonal noise; see oracle.h)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    dg = np.zeros(max(pb.m, 1), dtype=np.float64)
+    assert lib().oracle_diffusion_diag_derivative(ctypes.byref(pb), t, _ptr(x), _ptr(p), _ptr(dg)) == 0
+    return dg[:pb.m]
 
 
 def integrate(pb, params, x0, orbit_begin=0, k_begin=0, k_end=None, frames=True, nthreads=1):

@@ -139,6 +139,7 @@ int oracle_check_problem(const oracle_problem *pb)
 {
     int n = pb->n, m = pb->m, d = pb->d;
     if (n <= 0 || m < 0 || d <= 0) return -1;
+    if (pb->milstein != 0 && pb->milstein != 1) return -1;
     switch (pb->model) {
     case ORACLE_KURAMOTO:       return (m == n && d == n + 2) ? 0 : -1;
     case ORACLE_KURAMOTO_PAPER: return (m == n && d == 2 * n + 1) ? 0 : -1;
@@ -243,12 +244,36 @@ int oracle_diffusion(const oracle_problem *pb, double t, const double *x, const 
     }
 }
 
+/* d g_jj / d x_j of each model's diagonal noise (see oracle.h), written out
+ * from the diffusion above. */
+int oracle_diffusion_diag_derivative(const oracle_problem *pb, double t, const double *x, const double *p,
+                                     double *dg)
+{
+    (void)t;
+    (void)x;
+    int m = pb->m;
+    for (int j = 0; j < m; ++j) dg[j] = 0.0;
+    switch (pb->model) {
+    case ORACLE_KURAMOTO:        /* additive: g_jj = sigma */
+    case ORACLE_KURAMOTO_PAPER:  /* additive: g_jj = p_j */
+    case ORACLE_OU:              /* additive */
+    case ORACLE_LINEAR_ODE:      /* no noise */
+        return 0;
+    case ORACLE_FHN_NET:         /* g_jj = sigma v_j, channel j drives v_j = x_j */
+    case ORACLE_GBM:             /* g_jj = sigma x_j */
+        for (int j = 0; j < m; ++j) dg[j] = pb->model == ORACLE_GBM ? p[1] : p[5];
+        return 0;
+    default:
+        return -1;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
-/* Euler-Maruyama, Eq. 2.                                                    */
+/* Euler-Maruyama, Eq. 2, and the Milstein step.                             */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    double *f, *g, *N, *xn;
+    double *f, *g, *N, *xn, *dg;
 } em_scratch;
 
 static int scratch_alloc(em_scratch *s, int n, int m)
@@ -257,12 +282,13 @@ static int scratch_alloc(em_scratch *s, int n, int m)
     s->g = (double *)malloc(sizeof(double) * (size_t)(n * (m > 0 ? m : 1)));
     s->N = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     s->xn = (double *)malloc(sizeof(double) * (size_t)n);
-    return (s->f && s->g && s->N && s->xn) ? 0 : -1;
+    s->dg = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    return (s->f && s->g && s->N && s->xn && s->dg) ? 0 : -1;
 }
 
 static void scratch_free(em_scratch *s)
 {
-    free(s->f); free(s->g); free(s->N); free(s->xn);
+    free(s->f); free(s->g); free(s->N); free(s->xn); free(s->dg);
 }
 
 /* One step of Eq. 2 at step index k (reading of Eq. 2's t: the drift and
@@ -283,6 +309,14 @@ static void em_step(const oracle_problem *pb, const double *p, int64_t k, uint32
         double noise = 0.0;
         for (int j = 0; j < m; ++j) noise += s->g[i * m + j] * sqdt * s->N[j];
         s->xn[i] = x[i] + s->f[i] * pb->dt + noise;
+    }
+    if (pb->milstein && m > 0) {
+        /* channel j drives component j: + 1/2 g_jj g_jj' (dW_j^2 - dt) */
+        oracle_diffusion_diag_derivative(pb, t, x, p, s->dg);
+        for (int j = 0; j < m; ++j) {
+            double dW = sqdt * s->N[j];
+            s->xn[j] += 0.5 * s->g[j * m + j] * s->dg[j] * (dW * dW - pb->dt);
+        }
     }
     memcpy(x, s->xn, sizeof(double) * (size_t)n);
 }

@@ -43,6 +43,7 @@ typedef struct {
     uint64_t seed;           /* Philox key for the Wiener increments */
     int32_t shared_params;   /* 1: params is a single vector [d] used by every orbit */
     int32_t mean_field;      /* Kuramoto only: 1 = drift via (C, S) sums, 0 = pairwise definition */
+    int32_t milstein;        /* 1: Milstein step instead of Euler-Maruyama (diagonal noise) */
 } oracle_problem;
 
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel
@@ -76,6 +77,16 @@ void oracle_normals(uint64_t seed, uint32_t k, uint32_t orbit, int32_t m, double
  * major) of Eq. 1.  Return 0, or -1 for an unknown model. */
 int oracle_drift(const oracle_problem *pb, double t, const double *x, const double *p, double *f);
 int oracle_diffusion(const oracle_problem *pb, double t, const double *x, const double *p, double *g);
+
+/* Milstein scheme support (the paper names the Milstein method as the next
+ * integration scheme to add, Sec. 1.3 and Sec. 4; the scheme is Kloeden and
+ * Platen's, "Numerical Solution of Stochastic Differential Equations",
+ * Sec. 10.3).  Every model here has diagonal noise whose channel j drives
+ * state component j alone with g_jj a function of x_j only; dg[j] is
+ * d g_jj / d x_j for j < m.  The Milstein step adds, to component j,
+ *   1/2 g_jj dg_jj/dx_j (dW_j^2 - dt),   dW_j = sqrt(dt) N_j. */
+int oracle_diffusion_diag_derivative(const oracle_problem *pb, double t, const double *x, const double *p,
+                                     double *dg);
 
 /* Check n, m, d against the model; 0 = consistent. */
 int oracle_check_problem(const oracle_problem *pb);
