@@ -12,8 +12,10 @@ end-to-end value through the C ABI with pinned host buffers (host->device
 inputs and device->host frames inside the timed region), a roofline entry
 for the dominant kernel (the forward Euler-Maruyama kernel, bound by the
 SFU / special-function pipe), the same workload in FP64 on a 1000-step
-prefix of the horizon, and the CPU oracle timed on this host's cores on a
-bounded sample.
+prefix of the horizon, the discrete adjoint against its forward, the
+batched heterogeneous workload, the FitzHugh-Nagumo network under
+Euler-Maruyama and Milstein, and the CPU oracle timed on this host's cores
+on a bounded sample.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -343,6 +345,11 @@ def run_ours(args):
     if not args.no_adjoint:
         adjoint = _time_adjoint(stream, rank)
 
+    # ---- FitzHugh-Nagumo network, Euler-Maruyama and Milstein ------------
+    fhn = None
+    if not args.no_fhn:
+        fhn = _time_fhn(stream, rank)
+
     # ---- batched heterogeneous instances (one persistent graph launch) -----
     batched = None
     if not args.no_batched:
@@ -375,7 +382,8 @@ def run_ours(args):
                          "traffic_note": "DRAM bytes of the n=32 launch (ncu); algorithmic 3.52e9",
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
-            "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "fhn": fhn, "cpu_baseline": cpu,
+            "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -420,6 +428,47 @@ def _time_batch(stream, rank, reps=5):
             "ms": ms, "orbit_steps_per_sec": orbit_steps / (ms / 1e3), "osc_steps_per_sec": osc_steps / (ms / 1e3),
             "sfu_roofline_frac": SFU_OPS_PER_OSC_STEP * osc_steps / (ms / 1e3) / peak,
             "total_osc_steps": osc_steps, "longest_instance_osc_steps": longest, "schedule": info}
+
+
+def _time_fhn(stream, rank, reps=3, steps=10000):
+    """The FitzHugh-Nagumo network workload (64 units, n = 128, 2^18 orbits,
+    dt = 0.01, frame every 1000 steps), FP32, on the first 10^4 of its 10^5
+    steps (the cost per step is constant), Euler-Maruyama and Milstein."""
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import Integrator
+    from paper_1908_03869_gb300.sharding import weak_scaling_offset
+
+    W = inputs.WORKLOADS["fhn_64units"]
+    n, orbits = W["n"], W["orbits"]
+    p, x0 = inputs.fhn(n // 2, orbits, seed=1 + rank)
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    xt = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    out = {"workload": "FitzHugh-Nagumo network, 64 units (n = 128), 2^18 orbits, dt = 0.01, first %d of the "
+                       "10^5 steps, frame every %d steps, fp32" % (steps, W["stride"])}
+    unit_steps = orbits * (n // 2) * steps
+    for name, mil in (("euler_maruyama", False), ("milstein", True)):
+        pb = sdeb.Problem.make("fhn_net", n, orbits, W["dt"], steps, W["stride"], W["seed"], "fp32",
+                               orbit_offset=weak_scaling_offset(orbits, rank), milstein=mil)
+        times = []
+        with Integrator(pb) as it:
+            for _ in range(reps + 1):
+                it.set_params(pt, xt, stream=stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                it.integrate(stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+        ms = statistics.median(times[1:])
+        out[name] = {"ms": ms, "unit_steps_per_sec": unit_steps / (ms / 1e3)}
+    out["milstein_time_over_em"] = out["milstein"]["ms"] / out["euler_maruyama"]["ms"]
+    peak = SFU_PER_SM_PER_CLK * NUM_SMS * SM_MAX_MHZ * 1e6
+    # one normal per unit-step: half of (log2, sqrt, sin, cos) = 2 SFU operations
+    out["sfu_roofline_frac_em"] = 2.0 * out["euler_maruyama"]["unit_steps_per_sec"] / peak
+    return out
 
 
 def _time_adjoint(stream, rank, reps=5):
@@ -497,6 +546,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-fhn", action="store_true")
     ap.add_argument("--orbit-scale", type=float, default=1.0,
                     help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
     ap.add_argument("--horizon", type=int, default=None,

@@ -96,7 +96,17 @@ enum { SDEB_FP32_KAHAN = 0, SDEB_FP64 = 1 };
 /* Problem flags. */
 enum {
     SDEB_FLAG_SHARED_PARAMS = 1u, /* one parameter vector [d] for every orbit */
-    SDEB_FLAG_NO_FRAMES = 2u      /* keep only the final state (no frame buffer) */
+    SDEB_FLAG_NO_FRAMES = 2u,     /* keep only the final state (no frame buffer) */
+    /* Milstein step instead of Euler-Maruyama (the scheme the paper names as
+     * the next one to add, Sec. 1.3 and Sec. 4; Kloeden and Platen's form
+     * for diagonal noise): each Wiener channel j drives one state component
+     * x_j with g_j(x_j), and the step adds 1/2 g_j g_j' (dW_j^2 - dt), dW_j =
+     * sqrt(dt) N_j, to x_j.  This changes SDEB_GBM (g = sigma x) and the v
+     * components of SDEB_FHN_NET (g = sigma v); the Kuramoto models and
+     * SDEB_OU have additive noise and SDEB_LINEAR_ODE none, where Milstein
+     * and Euler-Maruyama coincide.  Same noise, checkpoints and resume as
+     * Euler-Maruyama; sdeb_grad stays the Kuramoto adjoint. */
+    SDEB_FLAG_MILSTEIN = 4u
 };
 
 typedef struct {

@@ -316,9 +316,15 @@ using KuramotoScalarLane = KuramotoLane<Real, P, false>;
 template <typename Real, int P>
 using KuramotoPaperLane = KuramotoLane<Real, P, true>;
 template <typename Real, int P>
+using FhnEmLane = FhnLane<Real, P, false>;
+template <typename Real, int P>
+using FhnMilsteinLane = FhnLane<Real, P, true>;
+template <typename Real, int P>
 using OuLane = ScalarLane<Real, P, 0>;
 template <typename Real, int P>
 using GbmLane = ScalarLane<Real, P, 1>;
+template <typename Real, int P>
+using GbmMilsteinLane = ScalarLane<Real, P, 1, true>;
 template <typename Real, int P>
 using LinearLane = ScalarLane<Real, P, 2>;
 

@@ -44,6 +44,7 @@ struct ForwardArgs {
     double dt;
     uint8_t *flags;  // [orbits]
     PhiloxKeys keys;
+    int32_t milstein;  // 1: Milstein step (models with multiplicative noise), 0: Euler-Maruyama
 };
 
 // Returns cudaSuccess or the launch error; cudaErrorNotSupported when the

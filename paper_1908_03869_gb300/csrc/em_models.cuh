@@ -73,14 +73,25 @@ struct KuramotoLane {
     }
 };
 
+// Milstein correction for diagonal noise whose channel drives one component
+// with g = s x (multiplicative): 1/2 g g' (dW^2 - dt) = 1/2 (s sqrt(dt))^2 x (N^2 - 1).
+// (The Milstein scheme, named by the paper as the next integrator in
+// Sec. 1.3 and Sec. 4; Kloeden and Platen's form for diagonal noise.)
+template <typename Real>
+__device__ __forceinline__ Real milstein_multiplicative(Real half_gsq2, Real x, Real N) {
+    return half_gsq2 * x * (N * N - Real(1));
+}
+
 // FitzHugh-Nagumo network: unit j has v_j = x[j], w_j = x[units + j];
 // p = (a, b, eps, I, c, sigma); multiplicative noise sigma v_j dW_j on v only.
-template <typename Real, int P>
+// MIL: Milstein step (adds 1/2 g g' (dW^2 - dt) to v) instead of Euler-Maruyama.
+template <typename Real, int P, bool MIL>
 struct FhnLane {
     static constexpr int U = 2;
     static constexpr int NR = 1;
     static constexpr bool kNoise = true;
     Real a, b, eps, I, c, gsq, dt, inv_units;
+    Real half_gsq2;  // (sigma sqrt(dt))^2 / 2, the Milstein coefficient
 
     __device__ __forceinline__ void load(const Real *p, int, int units, Real dt_, Real sqdt) {
         a = p[0];
@@ -91,6 +102,7 @@ struct FhnLane {
         gsq = p[5] * sqdt;
         dt = dt_;
         inv_units = Real(1) / (Real)units;
+        half_gsq2 = Real(0.5) * gsq * gsq;
     }
 
     __device__ __forceinline__ void prepare(const Real (&x)[U][P], const Real (&)[U][P], int u0, int units,
@@ -109,23 +121,27 @@ struct FhnLane {
         Real fv = v - v * v * v * Real(1.0 / 3.0) - w + I + c * mean_v - c * v;
         Real fw = eps * (v + a - b * w);
         inc[0] = fv * dt + gsq * v * N;
+        if constexpr (MIL) inc[0] += milstein_multiplicative(half_gsq2, v, N);
         inc[1] = fw * dt;
     }
 };
 
 // Ornstein-Uhlenbeck (KIND 0), geometric Brownian motion (KIND 1) and the
-// linear ODE (KIND 2, no noise): componentwise, no coupling.
-template <typename Real, int P, int KIND>
+// linear ODE (KIND 2, no noise): componentwise, no coupling.  MIL: Milstein
+// step; only GBM's multiplicative noise has a correction (OU's noise is
+// additive, where Milstein equals Euler-Maruyama).
+template <typename Real, int P, int KIND, bool MIL = false>
 struct ScalarLane {
     static constexpr int U = 1;
     static constexpr int NR = 0;
     static constexpr bool kNoise = KIND != 2;
-    Real rate, gsq, dt;
+    Real rate, gsq, dt, half_gsq2;
 
     __device__ __forceinline__ void load(const Real *p, int, int, Real dt_, Real sqdt) {
         rate = p[0];
         gsq = KIND == 2 ? Real(0) : p[1] * sqdt;
         dt = dt_;
+        half_gsq2 = Real(0.5) * gsq * gsq;
     }
 
     __device__ __forceinline__ void prepare(const Real (&)[U][P], const Real (&)[U][P], int, int,
@@ -135,7 +151,10 @@ struct ScalarLane {
                                          Real N, Real (&inc)[U]) const {
         Real xi = x[0][i];
         if (KIND == 0) inc[0] = -rate * xi * dt + gsq * N;
-        if (KIND == 1) inc[0] = rate * xi * dt + gsq * xi * N;
+        if (KIND == 1) {
+            inc[0] = rate * xi * dt + gsq * xi * N;
+            if constexpr (MIL) inc[0] += milstein_multiplicative(half_gsq2, xi, N);
+        }
         if (KIND == 2) inc[0] = -rate * xi * dt;
     }
 };

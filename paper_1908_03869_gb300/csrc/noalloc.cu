@@ -153,6 +153,7 @@ extern "C" sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void
     a.dt = pb->dt;
     a.flags = flags;
     a.keys = philox_key_schedule(pb->seed);
+    a.milstein = (pb->flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     const bool phase = pb->model == SDEB_KURAMOTO || pb->model == SDEB_KURAMOTO_PAPER;
     e = phase ? (fp64 ? launch_forward_kuramoto_f64(a, layout, s) : launch_forward_kuramoto_f32(a, layout, s))
               : (fp64 ? launch_forward_other_f64(a, layout, s) : launch_forward_other_f32(a, layout, s));

@@ -147,7 +147,7 @@ sdeb_status validate(const sdeb_problem *pb, int32_t &units) {
     if (pb->precision != SDEB_FP32_KAHAN && pb->precision != SDEB_FP64)
         return fail(nullptr, SDEB_EINVAL, "unknown precision %d", pb->precision);
     if (pb->ckpt_every < 0) return fail(nullptr, SDEB_EINVAL, "ckpt_every must be >= 0");
-    if (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES))
+    if (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES | SDEB_FLAG_MILSTEIN))
         return fail(nullptr, SDEB_EINVAL, "unknown flag bits 0x%x", pb->flags);
     if (pb->reserved != 0) return fail(nullptr, SDEB_EINVAL, "reserved field must be 0");
     if (pb->orbit_offset < 0 || pb->orbit_offset + pb->orbits > 0x100000000LL)
@@ -719,6 +719,7 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
     a.dt = ctx->pb.dt;
     a.flags = ctx->d_flags;
     a.keys = philox_key_schedule(ctx->pb.seed);
+    a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     cudaError_t e = launch_forward(a, ctx->layout, ctx->pb.precision == SDEB_FP64, as_stream(stream));
     if (e == cudaErrorNotSupported)
         return fail(ctx, SDEB_EUNSUPPORTED, "no kernel for model %d with layout G=%d P=%d", a.model,
@@ -866,6 +867,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
         a.dt = ctx->pb.dt;
         a.flags = tf;
         a.keys = philox_key_schedule(ctx->pb.seed);
+        a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
         float ms = 0.0f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
             e = cudaMemcpyAsync(tx, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
