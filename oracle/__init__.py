@@ -37,6 +37,7 @@ class Problem(ctypes.Structure):
         ("shared_params", ctypes.c_int32),
         ("mean_field", ctypes.c_int32),
         ("milstein", ctypes.c_int32),
+        ("rk4", ctypes.c_int32),
     ]
 
 
@@ -81,10 +82,10 @@ def _ptr(a):
 
 
 def make_problem(model, n, m, d, dt, steps, stride=1, seed=0, t0=0.0,
-                 shared_params=False, mean_field=False, milstein=False):
+                 shared_params=False, mean_field=False, milstein=False, rk4=False):
     return Problem(MODELS[model] if isinstance(model, str) else int(model), n, m, d, float(t0),
                    float(dt), int(steps), int(stride), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                   int(bool(shared_params)), int(bool(mean_field)), int(bool(milstein)))
+                   int(bool(shared_params)), int(bool(mean_field)), int(bool(milstein)), int(bool(rk4)))
 
 
 def philox(ctr, key):

@@ -140,6 +140,8 @@ int oracle_check_problem(const oracle_problem *pb)
     int n = pb->n, m = pb->m, d = pb->d;
     if (n <= 0 || m < 0 || d <= 0) return -1;
     if (pb->milstein != 0 && pb->milstein != 1) return -1;
+    if (pb->rk4 != 0 && pb->rk4 != 1) return -1;
+    if (pb->milstein && pb->rk4) return -1;
     switch (pb->model) {
     case ORACLE_KURAMOTO:       return (m == n && d == n + 2) ? 0 : -1;
     case ORACLE_KURAMOTO_PAPER: return (m == n && d == 2 * n + 1) ? 0 : -1;
@@ -273,7 +275,7 @@ int oracle_diffusion_diag_derivative(const oracle_problem *pb, double t, const d
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    double *f, *g, *N, *xn, *dg;
+    double *f, *g, *N, *xn, *dg, *k[4], *y;
 } em_scratch;
 
 static int scratch_alloc(em_scratch *s, int n, int m)
@@ -283,12 +285,39 @@ static int scratch_alloc(em_scratch *s, int n, int m)
     s->N = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     s->xn = (double *)malloc(sizeof(double) * (size_t)n);
     s->dg = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
-    return (s->f && s->g && s->N && s->xn && s->dg) ? 0 : -1;
+    s->y = (double *)malloc(sizeof(double) * (size_t)n);
+    int ok = s->f && s->g && s->N && s->xn && s->dg && s->y;
+    for (int q = 0; q < 4; ++q) {
+        s->k[q] = (double *)malloc(sizeof(double) * (size_t)n);
+        ok = ok && s->k[q];
+    }
+    return ok ? 0 : -1;
 }
 
 static void scratch_free(em_scratch *s)
 {
-    free(s->f); free(s->g); free(s->N); free(s->xn); free(s->dg);
+    free(s->f); free(s->g); free(s->N); free(s->xn); free(s->dg); free(s->y);
+    for (int q = 0; q < 4; ++q) free(s->k[q]);
+}
+
+/* One step of the classical fourth-order Runge-Kutta method on the drift
+ * alone, dx/dt = f(t, x) (the ODE path; the paper lists Runge-Kutta among
+ * the ODE integrators, Sec. 1.2):
+ *   k1 = f(t, x), k2 = f(t + h/2, x + h k1/2), k3 = f(t + h/2, x + h k2/2),
+ *   k4 = f(t + h, x + h k3), x <- x + h (k1 + 2 k2 + 2 k3 + k4) / 6. */
+static void rk4_step(const oracle_problem *pb, const double *p, int64_t k, double *x, em_scratch *s)
+{
+    int n = pb->n;
+    double h = pb->dt, t = pb->t0 + (double)k * h;
+    oracle_drift(pb, t, x, p, s->k[0]);
+    for (int i = 0; i < n; ++i) s->y[i] = x[i] + 0.5 * h * s->k[0][i];
+    oracle_drift(pb, t + 0.5 * h, s->y, p, s->k[1]);
+    for (int i = 0; i < n; ++i) s->y[i] = x[i] + 0.5 * h * s->k[1][i];
+    oracle_drift(pb, t + 0.5 * h, s->y, p, s->k[2]);
+    for (int i = 0; i < n; ++i) s->y[i] = x[i] + h * s->k[2][i];
+    oracle_drift(pb, t + h, s->y, p, s->k[3]);
+    for (int i = 0; i < n; ++i)
+        x[i] += h * (s->k[0][i] + 2.0 * s->k[1][i] + 2.0 * s->k[2][i] + s->k[3][i]) / 6.0;
 }
 
 /* One step of Eq. 2 at step index k (reading of Eq. 2's t: the drift and
@@ -297,6 +326,10 @@ static void scratch_free(em_scratch *s)
 static void em_step(const oracle_problem *pb, const double *p, int64_t k, uint32_t orbit,
                     double *x, em_scratch *s)
 {
+    if (pb->rk4) {
+        rk4_step(pb, p, k, x, s);
+        return;
+    }
     int n = pb->n, m = pb->m;
     double t = pb->t0 + (double)k * pb->dt;
     double sqdt = sqrt(pb->dt);
@@ -504,7 +537,8 @@ int oracle_adjoint(const oracle_problem *pb, const double *params, const double 
                    int64_t orbit_begin, int64_t count, const double *dL_dxK,
                    double *dL_dp, double *dL_dx0)
 {
-    if (oracle_check_problem(pb) != 0 || count < 0 || pb->steps > 0xffffffffLL)
+    /* the adjoint of the Euler-Maruyama recursion only */
+    if (oracle_check_problem(pb) != 0 || count < 0 || pb->steps > 0xffffffffLL || pb->rk4 || pb->milstein)
         return -1;
     int n = pb->n, m = pb->m, d = pb->d;
     int64_t K = pb->steps;

@@ -44,6 +44,7 @@ typedef struct {
     int32_t shared_params;   /* 1: params is a single vector [d] used by every orbit */
     int32_t mean_field;      /* Kuramoto only: 1 = drift via (C, S) sums, 0 = pairwise definition */
     int32_t milstein;        /* 1: Milstein step instead of Euler-Maruyama (diagonal noise) */
+    int32_t rk4;             /* 1: classical fourth-order Runge-Kutta on the drift alone (ODE path) */
 } oracle_problem;
 
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel
