@@ -105,8 +105,18 @@ enum {
      * components of SDEB_FHN_NET (g = sigma v); the Kuramoto models and
      * SDEB_OU have additive noise and SDEB_LINEAR_ODE none, where Milstein
      * and Euler-Maruyama coincide.  Same noise, checkpoints and resume as
-     * Euler-Maruyama; sdeb_grad stays the Kuramoto adjoint. */
-    SDEB_FLAG_MILSTEIN = 4u
+     * Euler-Maruyama.  sdeb_grad returns EUNSUPPORTED (it is the adjoint
+     * of the Euler-Maruyama step). */
+    SDEB_FLAG_MILSTEIN = 4u,
+    /* The ODE path: classical fourth-order Runge-Kutta on the drift alone,
+     * dx/dt = f(t, x, p) (the paper lists Runge-Kutta among its ODE
+     * integrators, Sec. 1.2): k1 = h f(x), k2 = h f(x + k1/2), k3 = h f(x +
+     * k2/2), k4 = h f(x + k3), x += (k1 + 2 k2 + 2 k3 + k4) / 6.  The
+     * diffusion is not applied and no noise is drawn.  Every model, the
+     * layouts sdeb_create picks (sdeb_set_layout to another layout returns
+     * EUNSUPPORTED at integration).  Exclusive with SDEB_FLAG_MILSTEIN
+     * (EINVAL); sdeb_grad and batches return EUNSUPPORTED. */
+    SDEB_FLAG_RK4 = 8u
 };
 
 typedef struct {

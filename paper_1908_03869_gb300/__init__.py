@@ -20,6 +20,7 @@ __all__ = [
     "SDEB_EUNSUPPORTED", "SDEB_ENONFINITE",
     "SDEB_KURAMOTO", "SDEB_KURAMOTO_PAPER", "SDEB_FHN_NET", "SDEB_OU", "SDEB_GBM", "SDEB_LINEAR_ODE",
     "SDEB_FP32_KAHAN", "SDEB_FP64", "SDEB_FLAG_SHARED_PARAMS", "SDEB_FLAG_NO_FRAMES", "SDEB_FLAG_MILSTEIN",
+    "SDEB_FLAG_RK4",
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
@@ -31,7 +32,7 @@ __all__ = [
 SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
 SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER, SDEB_FHN_NET, SDEB_OU, SDEB_GBM, SDEB_LINEAR_ODE = range(1, 7)
 SDEB_FP32_KAHAN, SDEB_FP64 = 0, 1
-SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES, SDEB_FLAG_MILSTEIN = 1, 2, 4
+SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES, SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4 = 1, 2, 4, 8
 
 MODEL_IDS = {
     "kuramoto": SDEB_KURAMOTO, "kuramoto_paper": SDEB_KURAMOTO_PAPER, "fhn_net": SDEB_FHN_NET,
@@ -61,11 +62,11 @@ class Problem(ctypes.Structure):
 
     @classmethod
     def make(cls, model, n, orbits, dt, steps, stride=1, seed=0, precision="fp32", t0=0.0, ckpt_every=0,
-             shared_params=False, no_frames=False, orbit_offset=0, m=None, d=None, milstein=False):
+             shared_params=False, no_frames=False, orbit_offset=0, m=None, d=None, milstein=False, rk4=False):
         mid = MODEL_IDS.get(model, model)
         m0, d0 = model_shape(mid, n) if mid in MODEL_IDS.values() else (0, 0)
         flags = (SDEB_FLAG_SHARED_PARAMS if shared_params else 0) | (SDEB_FLAG_NO_FRAMES if no_frames else 0) | \
-            (SDEB_FLAG_MILSTEIN if milstein else 0)
+            (SDEB_FLAG_MILSTEIN if milstein else 0) | (SDEB_FLAG_RK4 if rk4 else 0)
         return cls(mid, n, m0 if m is None else m, d0 if d is None else d, orbits, t0, dt, steps, stride,
                    seed & 0xFFFFFFFFFFFFFFFF, PRECISIONS.get(precision, precision), ckpt_every, flags, 0,
                    orbit_offset)

@@ -160,7 +160,62 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
     }
 }
 
-template <class M, typename Real, int G, int P>
+// One stage of the classical fourth-order Runge-Kutta step (below): the
+// coupling sums at `at` (with compensation words ca), then per unit the
+// model's increment with a zero normal, h f(at); acc += weight h f(at), and
+// y = base + frac_next h f(at) is the next stage's state (y may be `at`:
+// each unit is read before it is overwritten, the sums were taken first).
+template <class M, typename Real, int P, class RED>
+__device__ __forceinline__ void rk4_stage(M &model, const Real (&at)[M::U][P], const Real (&ca)[M::U][P],
+                                          const Real (&base)[M::U][P], int u0, int units, RED &reduce,
+                                          Real (&acc)[M::U][P], Real (&y)[M::U][P], Real weight, Real frac_next) {
+    constexpr int NRA = M::NR > 0 ? M::NR : 1;
+    Real red[NRA];
+    model.prepare(at, ca, u0, units, red);
+    if constexpr (M::NR > 0) reduce(red);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        Real inc[M::U];
+        model.incr(i, at, red, Real(0), inc);
+#pragma unroll
+        for (int c = 0; c < M::U; ++c) {
+            acc[c][i] = fma_r(weight, inc[c], acc[c][i]);
+            y[c][i] = fma_r(frac_next, inc[c], base[c][i]);
+        }
+    }
+}
+
+// One step of the classical fourth-order Runge-Kutta method on the drift
+// alone (the ODE path; the paper lists Runge-Kutta among its ODE
+// integrators, Sec. 1.2): stages at x, x + k1/2, x + k2/2, x + k3 with
+// k = h f, and (k1 + 2 k2 + 2 k3 + k4) / 6 goes through the same compensated
+// accumulation as an Euler-Maruyama increment.  No noise is drawn.  The
+// stage states are built on the model's stage base (for the phase models
+// the compensated phase reduced to [-pi, pi], so a stage phase carries the
+// rounding of a number below pi rather than of the unreduced phase).
+template <class M, typename Real, int P, class RED>
+__device__ __forceinline__ void rk4_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], int u0, int units,
+                                         RED &reduce) {
+    Real acc[M::U][P], y[M::U][P], base[M::U][P], none[M::U][P];
+#pragma unroll
+    for (int c = 0; c < M::U; ++c)
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            acc[c][i] = Real(0);
+            none[c][i] = Real(0);
+        }
+    model.stage_base(x, cp, base);
+    rk4_stage<M, Real, P>(model, x, cp, base, u0, units, reduce, acc, y, Real(1), Real(0.5));
+    rk4_stage<M, Real, P>(model, y, none, base, u0, units, reduce, acc, y, Real(2), Real(0.5));
+    rk4_stage<M, Real, P>(model, y, none, base, u0, units, reduce, acc, y, Real(2), Real(1));
+    rk4_stage<M, Real, P>(model, y, none, base, u0, units, reduce, acc, y, Real(1), Real(0));
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], mul_r(acc[c][i], Real(1) / Real(6)));
+}
+
+template <class M, typename Real, int G, int P, bool RK4>
 __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     constexpr int U = M::U;
     constexpr bool kKahan = std::is_same<Real, float>::value;
@@ -209,7 +264,12 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
         if (ckpt != nullptr) k_stop = min(k_stop, (uint64_t)k + to_ckpt);
         const uint32_t run = (uint32_t)(k_stop - k);
 #pragma unroll kRunUnroll
-        for (uint32_t s = 0; s < run; ++s) em_step<M, Real, P>(model, x, cp, k + s, gorb, u0, units, a.keys, reduce);
+        for (uint32_t s = 0; s < run; ++s) {
+            if constexpr (RK4)
+                rk4_step<M, Real, P>(model, x, cp, u0, units, reduce);
+            else
+                em_step<M, Real, P>(model, x, cp, k + s, gorb, u0, units, a.keys, reduce);
+        }
         k += run;
         if (frames != nullptr && (to_frame -= run) == 0) {
             to_frame = a.stride;
@@ -249,9 +309,9 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     }
 }
 
-template <class M, typename Real, int G, int P>
+template <class M, typename Real, int G, int P, bool RK4>
 __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const ForwardArgs a) {
-    em_forward_body<M, Real, G, P>(a);
+    em_forward_body<M, Real, G, P, RK4>(a);
 }
 
 // The same kernel with registers capped so that five blocks fit per SM: used
@@ -261,27 +321,31 @@ __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const Forward
 // layouts keep the compiler's choice (96 registers already).
 template <class M, typename Real, int G, int P>
 __global__ void __launch_bounds__(kForwardBlock, 5) em_forward_kernel_5blocks(const ForwardArgs a) {
-    em_forward_body<M, Real, G, P>(a);
+    em_forward_body<M, Real, G, P, false>(a);
 }
 
 template <class M, typename Real, int G, int P>
 constexpr bool kForwardFiveBlocks = std::is_same<Real, float>::value && G > 1 && M::U == 1 && P <= 8;
 
-template <template <typename, int> class MF, typename Real, int G, int P>
+// RK4: the Runge-Kutta instantiation (the ODE path), else Euler-Maruyama or
+// Milstein (chosen by the model functor).
+template <template <typename, int> class MF, typename Real, int G, int P, bool RK4 = false>
 cudaError_t launch_forward_layout(const ForwardArgs &a, cudaStream_t s) {
     using M = MF<Real, P>;
     const int64_t threads = a.orbits * G;
     const int64_t grid = (threads + kForwardBlock - 1) / kForwardBlock;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if constexpr (kForwardFiveBlocks<M, Real, G, P>)
+    if constexpr (!RK4 && kForwardFiveBlocks<M, Real, G, P>)
         em_forward_kernel_5blocks<M, Real, G, P><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     else
-        em_forward_kernel<M, Real, G, P><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
+        em_forward_kernel<M, Real, G, P, RK4><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 #define SDEB_FORWARD_LAYOUT(G_, P_) \
     if (l.G == (G_) && l.P == (P_)) return launch_forward_layout<MF, Real, G_, P_>(a, s);
+#define SDEB_FORWARD_LAYOUT_RK4(G_, P_) \
+    if (l.G == (G_) && l.P == (P_)) return launch_forward_layout<MF, Real, G_, P_, true>(a, s);
 
 // The layouts default_layout() can return.
 template <template <typename, int> class MF, typename Real>
@@ -295,6 +359,21 @@ cudaError_t dispatch_default_layouts(const ForwardArgs &a, Layout l, cudaStream_
     SDEB_FORWARD_LAYOUT(8, 8)
     SDEB_FORWARD_LAYOUT(16, 8)
     SDEB_FORWARD_LAYOUT(32, 8)
+    return cudaErrorNotSupported;
+}
+
+// The Runge-Kutta instantiations, for the layouts default_layout() can return.
+template <template <typename, int> class MF, typename Real>
+cudaError_t dispatch_rk4_layouts(const ForwardArgs &a, Layout l, cudaStream_t s) {
+    SDEB_FORWARD_LAYOUT_RK4(1, 1)
+    SDEB_FORWARD_LAYOUT_RK4(1, 2)
+    SDEB_FORWARD_LAYOUT_RK4(1, 4)
+    SDEB_FORWARD_LAYOUT_RK4(1, 8)
+    SDEB_FORWARD_LAYOUT_RK4(2, 8)
+    SDEB_FORWARD_LAYOUT_RK4(4, 8)
+    SDEB_FORWARD_LAYOUT_RK4(8, 8)
+    SDEB_FORWARD_LAYOUT_RK4(16, 8)
+    SDEB_FORWARD_LAYOUT_RK4(32, 8)
     return cudaErrorNotSupported;
 }
 

@@ -45,6 +45,7 @@ struct ForwardArgs {
     uint8_t *flags;  // [orbits]
     PhiloxKeys keys;
     int32_t milstein;  // 1: Milstein step (models with multiplicative noise), 0: Euler-Maruyama
+    int32_t rk4;       // 1: fourth-order Runge-Kutta on the drift alone (launch_forward_rk4_*)
 };
 
 // Returns cudaSuccess or the launch error; cudaErrorNotSupported when the
@@ -53,6 +54,16 @@ cudaError_t launch_forward_kuramoto_f32(const ForwardArgs &a, Layout l, cudaStre
 cudaError_t launch_forward_kuramoto_f64(const ForwardArgs &a, Layout l, cudaStream_t s);
 cudaError_t launch_forward_other_f32(const ForwardArgs &a, Layout l, cudaStream_t s);
 cudaError_t launch_forward_other_f64(const ForwardArgs &a, Layout l, cudaStream_t s);
+cudaError_t launch_forward_rk4_f32(const ForwardArgs &a, Layout l, cudaStream_t s);
+cudaError_t launch_forward_rk4_f64(const ForwardArgs &a, Layout l, cudaStream_t s);
+
+// The forward launch of a problem: Runge-Kutta, phase models or the others.
+inline cudaError_t launch_forward_any(const ForwardArgs &a, Layout l, bool fp64, cudaStream_t s) {
+    if (a.rk4) return fp64 ? launch_forward_rk4_f64(a, l, s) : launch_forward_rk4_f32(a, l, s);
+    const bool phase = a.model == kKuramoto || a.model == kKuramotoPaper;
+    if (phase) return fp64 ? launch_forward_kuramoto_f64(a, l, s) : launch_forward_kuramoto_f32(a, l, s);
+    return fp64 ? launch_forward_other_f64(a, l, s) : launch_forward_other_f32(a, l, s);
+}
 
 // Arguments of the discrete-adjoint launch (Kuramoto models).
 struct AdjointArgs {

@@ -50,6 +50,15 @@ struct KuramotoLane {
         }
     }
 
+    // Base of the Runge-Kutta stage states: the compensated phase reduced to
+    // [-pi, pi] (sin and cos are 2 pi periodic; the stages see the phase
+    // with the rounding of a number below pi).
+    __device__ __forceinline__ void stage_base(const Real (&x)[U][P], const Real (&cp)[U][P],
+                                               Real (&base)[U][P]) const {
+#pragma unroll
+        for (int i = 0; i < P; ++i) base[0][i] = reduce_phase(x[0][i], cp[0][i]);
+    }
+
     // Padding units enter the sums with weight 0: fma(1, v, s) == s + v.
     __device__ __forceinline__ void prepare(const Real (&x)[U][P], const Real (&cp)[U][P], int, int,
                                             Real (&red)[NR]) {
@@ -92,6 +101,15 @@ struct FhnLane {
     static constexpr bool kNoise = true;
     Real a, b, eps, I, c, gsq, dt, inv_units;
     Real half_gsq2;  // (sigma sqrt(dt))^2 / 2, the Milstein coefficient
+
+    // Base of the Runge-Kutta stage states: the state itself.
+    __device__ __forceinline__ void stage_base(const Real (&x)[U][P], const Real (&)[U][P],
+                                               Real (&base)[U][P]) const {
+#pragma unroll
+        for (int c = 0; c < U; ++c)
+#pragma unroll
+            for (int i = 0; i < P; ++i) base[c][i] = x[c][i];
+    }
 
     __device__ __forceinline__ void load(const Real *p, int, int units, Real dt_, Real sqdt) {
         a = p[0];
@@ -136,6 +154,13 @@ struct ScalarLane {
     static constexpr int NR = 0;
     static constexpr bool kNoise = KIND != 2;
     Real rate, gsq, dt, half_gsq2;
+
+    // Base of the Runge-Kutta stage states: the state itself.
+    __device__ __forceinline__ void stage_base(const Real (&x)[U][P], const Real (&)[U][P],
+                                               Real (&base)[U][P]) const {
+#pragma unroll
+        for (int i = 0; i < P; ++i) base[0][i] = x[0][i];
+    }
 
     __device__ __forceinline__ void load(const Real *p, int, int, Real dt_, Real sqdt) {
         rate = p[0];

@@ -147,8 +147,10 @@ sdeb_status validate(const sdeb_problem *pb, int32_t &units) {
     if (pb->precision != SDEB_FP32_KAHAN && pb->precision != SDEB_FP64)
         return fail(nullptr, SDEB_EINVAL, "unknown precision %d", pb->precision);
     if (pb->ckpt_every < 0) return fail(nullptr, SDEB_EINVAL, "ckpt_every must be >= 0");
-    if (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES | SDEB_FLAG_MILSTEIN))
+    if (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES | SDEB_FLAG_MILSTEIN | SDEB_FLAG_RK4))
         return fail(nullptr, SDEB_EINVAL, "unknown flag bits 0x%x", pb->flags);
+    if ((pb->flags & SDEB_FLAG_MILSTEIN) && (pb->flags & SDEB_FLAG_RK4))
+        return fail(nullptr, SDEB_EINVAL, "SDEB_FLAG_MILSTEIN and SDEB_FLAG_RK4 are exclusive");
     if (pb->reserved != 0) return fail(nullptr, SDEB_EINVAL, "reserved field must be 0");
     if (pb->orbit_offset < 0 || pb->orbit_offset + pb->orbits > 0x100000000LL)
         return fail(nullptr, SDEB_EINVAL, "orbit_offset + orbits must not exceed 2^32");
@@ -173,9 +175,7 @@ bool layout_instantiated(int32_t model, Layout l) {
 }
 
 cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream_t s) {
-    const bool phase = a.model == kKuramoto || a.model == kKuramotoPaper;
-    if (phase) return fp64 ? launch_forward_kuramoto_f64(a, l, s) : launch_forward_kuramoto_f32(a, l, s);
-    return fp64 ? launch_forward_other_f64(a, l, s) : launch_forward_other_f32(a, l, s);
+    return launch_forward_any(a, l, fp64, s);
 }
 
 // ---- batch planning ---------------------------------------------------------
@@ -513,6 +513,8 @@ sdeb_status build_batch_instances(const sdeb_problem *pbs, int32_t count, std::v
         if (pb.precision != pbs[0].precision || pb.seed != pbs[0].seed)
             return fail(nullptr, SDEB_EINVAL, "instance %d: precision and seed must match instance 0", i);
         if (pb.ckpt_every != 0) return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: no checkpoints in a batch", i);
+        if (pb.flags & SDEB_FLAG_RK4)
+            return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: batches run Euler-Maruyama", i);
         if (pb.orbits > 0x7fffffffLL) return fail(nullptr, SDEB_EINVAL, "instance %d: too many orbits", i);
         const bool shared = pb.flags & SDEB_FLAG_SHARED_PARAMS;
         const bool frames = !(pb.flags & SDEB_FLAG_NO_FRAMES);
@@ -720,6 +722,7 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
     a.flags = ctx->d_flags;
     a.keys = philox_key_schedule(ctx->pb.seed);
     a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
+    a.rk4 = (ctx->pb.flags & SDEB_FLAG_RK4) ? 1 : 0;
     cudaError_t e = launch_forward(a, ctx->layout, ctx->pb.precision == SDEB_FP64, as_stream(stream));
     if (e == cudaErrorNotSupported)
         return fail(ctx, SDEB_EUNSUPPORTED, "no kernel for model %d with layout G=%d P=%d", a.model,
@@ -821,7 +824,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
     // A context that keeps checkpoints for sdeb_grad is tuned for forward +
     // adjoint: both are timed over one segment (at most 1024 steps) from
     // checkpoint 0, which sdeb_set_params has written.
-    const bool tune_adjoint = ctx->d_seg != nullptr;
+    const bool tune_adjoint = ctx->d_seg != nullptr && !(ctx->pb.flags & (SDEB_FLAG_RK4 | SDEB_FLAG_MILSTEIN));
     if (trial_steps <= 0) trial_steps = 64;
     if (tune_adjoint) trial_steps = std::min<int64_t>((int64_t)ctx->pb.ckpt_every, 1024);
     if (trial_steps > ctx->pb.steps) trial_steps = ctx->pb.steps;
@@ -868,6 +871,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
         a.flags = tf;
         a.keys = philox_key_schedule(ctx->pb.seed);
         a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
+        a.rk4 = (ctx->pb.flags & SDEB_FLAG_RK4) ? 1 : 0;
         float ms = 0.0f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
             e = cudaMemcpyAsync(tx, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
@@ -956,6 +960,8 @@ sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_d
     if (ctx->pb.model != SDEB_KURAMOTO && ctx->pb.model != SDEB_KURAMOTO_PAPER)
         return fail(ctx, SDEB_EUNSUPPORTED, "the adjoint is implemented for the Kuramoto models");
     if (ctx->pb.ckpt_every <= 0) return fail(ctx, SDEB_ESTATE, "context was created with ckpt_every = 0");
+    if (ctx->pb.flags & (SDEB_FLAG_RK4 | SDEB_FLAG_MILSTEIN))
+        return fail(ctx, SDEB_EUNSUPPORTED, "sdeb_grad is the adjoint of the Euler-Maruyama step");
     if (!ctx->params_set || ctx->k_current != ctx->pb.steps)
         return fail(ctx, SDEB_ESTATE, "integrate to step %lld first (state is at %lld)", (long long)ctx->pb.steps,
                     (long long)ctx->k_current);
