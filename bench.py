@@ -14,8 +14,8 @@ for the dominant kernel (the forward Euler-Maruyama kernel, bound by the
 SFU / special-function pipe), the same workload in FP64 on a 1000-step
 prefix of the horizon, the discrete adjoint against its forward, the
 batched heterogeneous workload, the FitzHugh-Nagumo network under
-Euler-Maruyama and Milstein, and the CPU oracle timed on this host's cores
-on a bounded sample.
+Euler-Maruyama and Milstein, the ODE path (fourth-order Runge-Kutta), and
+the CPU oracle timed on this host's cores on a bounded sample.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -350,6 +350,11 @@ def run_ours(args):
     if not args.no_fhn:
         fhn = _time_fhn(stream, rank)
 
+    # ---- the ODE path: fourth-order Runge-Kutta on the Kuramoto drift -------
+    rk4 = None
+    if not args.no_rk4:
+        rk4 = _time_rk4(stream, rank)
+
     # ---- batched heterogeneous instances (one persistent graph launch) -----
     batched = None
     if not args.no_batched:
@@ -382,7 +387,8 @@ def run_ours(args):
                          "traffic_note": "DRAM bytes of the n=32 launch (ncu); algorithmic 3.52e9",
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
-            "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "fhn": fhn, "cpu_baseline": cpu,
+            "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "fhn": fhn, "rk4": rk4,
+            "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
         }
@@ -471,6 +477,45 @@ def _time_fhn(stream, rank, reps=3, steps=10000):
     return out
 
 
+def _time_rk4(stream, rank, reps=3, steps=1000):
+    """The ODE path: classical fourth-order Runge-Kutta on the drift of the
+    n = 32 benchmark problem (2^18 orbits, dt = 0.005, frame every 100 steps),
+    FP32, first 1000 steps, beside Euler-Maruyama on the same steps."""
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import Integrator
+    from paper_1908_03869_gb300.sharding import weak_scaling_offset
+
+    n, orbits = 32, 1 << 18
+    p, x0 = inputs.kuramoto(n, orbits, seed=1 + rank)
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    xt = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    out = {"workload": "Kuramoto n = 32, 2^18 orbits, dt = %g, first %d steps, frame every %d steps, fp32"
+                       % (DT, steps, STRIDE)}
+    for name, rk in (("euler_maruyama", False), ("rk4", True)):
+        pb = sdeb.Problem.make("kuramoto", n, orbits, DT, steps, STRIDE, SEED, "fp32",
+                               orbit_offset=weak_scaling_offset(orbits, rank), rk4=rk)
+        times = []
+        with Integrator(pb) as it:
+            for _ in range(reps + 1):
+                it.set_params(pt, xt, stream=stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                it.integrate(stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+        ms = statistics.median(times[1:])
+        out[name] = {"ms": ms, "orbit_steps_per_sec": orbits * steps / (ms / 1e3)}
+    peak = SFU_PER_SM_PER_CLK * NUM_SMS * SM_MAX_MHZ * 1e6
+    # four drift evaluations per step, each a sin and a cos per oscillator
+    out["sfu_roofline_frac_rk4"] = 8.0 * n * out["rk4"]["orbit_steps_per_sec"] / peak
+    out["rk4_time_over_em"] = out["rk4"]["ms"] / out["euler_maruyama"]["ms"]
+    return out
+
+
 def _time_adjoint(stream, rank, reps=5):
     import ctypes
 
@@ -547,6 +592,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fhn", action="store_true")
+    ap.add_argument("--no-rk4", action="store_true")
     ap.add_argument("--orbit-scale", type=float, default=1.0,
                     help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
     ap.add_argument("--horizon", type=int, default=None,
