@@ -14,8 +14,9 @@ for the dominant kernel (the forward Euler-Maruyama kernel, bound by the
 SFU / special-function pipe), the same workload in FP64 on a 1000-step
 prefix of the horizon, the discrete adjoint against its forward, the
 batched heterogeneous workload, the FitzHugh-Nagumo network under
-Euler-Maruyama and Milstein, the ODE path (fourth-order Runge-Kutta), and
-the CPU oracle timed on this host's cores on a bounded sample.
+Euler-Maruyama and Milstein, the ODE path (fourth-order Runge-Kutta), the
+paper's own speed protocol in FP64, and the CPU oracle timed on this host's
+cores on a bounded sample.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -355,6 +356,11 @@ def run_ours(args):
     if not args.no_rk4:
         rk4 = _time_rk4(stream, rank)
 
+    # ---- the paper's own speed protocol (Sec. 2.2.1), FP64 -----------------
+    paper = None
+    if not args.no_paper_protocol:
+        paper = _time_paper_protocol(stream, rank)
+
     # ---- batched heterogeneous instances (one persistent graph launch) -----
     batched = None
     if not args.no_batched:
@@ -388,7 +394,7 @@ def run_ours(args):
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
             "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "fhn": fhn, "rk4": rk4,
-            "cpu_baseline": cpu,
+            "paper_speed_protocol": paper, "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
         }
@@ -474,6 +480,61 @@ def _time_fhn(stream, rank, reps=3, steps=10000):
     peak = SFU_PER_SM_PER_CLK * NUM_SMS * SM_MAX_MHZ * 1e6
     # one normal per unit-step: half of (log2, sqrt, sin, cos) = 2 SFU operations
     out["sfu_roofline_frac_em"] = 2.0 * out["euler_maruyama"]["unit_steps_per_sec"] / peak
+    return out
+
+
+# The paper's runtimes of its speed protocol on an NVIDIA P100 (Tables S1-S3,
+# M = 163840 orbits, FP64, including OpenCL set-up and host transfers): context
+# for the same protocol here, not a target.
+PAPER_P100_SECONDS = {5: 4.719, 10: 9.315, 15: 17.656}
+
+
+def _time_paper_protocol(stream, rank):
+    """The paper's speed protocol (Sec. 2.2.1): stochastic Kuramoto in the
+    paper's parameter layout p = (K, omega_1..omega_N, p_1..p_N), K = 1,
+    omega ~ U(0.01, 0.03), p ~ U(0.001, 0.003), theta(0) ~ U(-pi, pi),
+    N = 5 / 10 / 15 oscillators, M = 163840 orbits, dt = 0.05, T = 400 s
+    (8000 steps), FP64; a frame every 100 steps.  Device time of the whole
+    horizon, and end to end through the C ABI (host inputs in, all frames
+    to pinned host memory)."""
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import Integrator
+    from paper_1908_03869_gb300.sharding import weak_scaling_offset
+
+    orbits, dt, steps, stride = 163840, 0.05, 8000, 100
+    out = {"workload": "paper speed protocol: Kuramoto paper layout, M = 163840, dt = 0.05, 8000 steps, "
+                       "frame every 100 steps, fp64",
+           "paper_p100_seconds_context": PAPER_P100_SECONDS, "runs": {}}
+    for n in (5, 10, 15):
+        p, x0 = inputs.kuramoto_paper_speed(n, orbits, seed=1 + rank)
+        ph, xh = torch.tensor(p).pin_memory(), torch.tensor(x0).pin_memory()
+        pd, xd = ph.cuda(), xh.cuda()
+        pb = sdeb.Problem.make("kuramoto_paper", n, orbits, dt, steps, stride, 0, "fp64",
+                               orbit_offset=weak_scaling_offset(orbits, rank))
+        with Integrator(pb) as it:
+            host_frames = torch.empty((it.nframes, orbits, n), dtype=torch.float64, pin_memory=True)
+            it.set_params(pd, xd, stream=stream)
+            it.integrate_range(0, 100, stream=stream)          # warm-up
+            torch.cuda.synchronize()
+            it.set_params(pd, xd, stream=stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            it.integrate(stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dev_s = a.elapsed_time(b) / 1e3
+            t0 = time.perf_counter()
+            it.set_params(ph, xh, stream=stream)
+            it.integrate(stream=stream)
+            it.frames(out=host_frames, stream=stream)
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+        out["runs"][str(n)] = {"device_s": dev_s, "e2e_s": e2e_s,
+                               "orbit_steps_per_sec": orbits * steps / dev_s,
+                               "e2e_orbit_steps_per_sec": orbits * steps / e2e_s}
     return out
 
 
@@ -593,6 +654,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-fhn", action="store_true")
     ap.add_argument("--no-rk4", action="store_true")
+    ap.add_argument("--no-paper-protocol", action="store_true")
     ap.add_argument("--orbit-scale", type=float, default=1.0,
                     help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
     ap.add_argument("--horizon", type=int, default=None,
