@@ -15,8 +15,8 @@ SFU / special-function pipe), the same workload in FP64 on a 1000-step
 prefix of the horizon, the discrete adjoint against its forward, the
 batched heterogeneous workload, the FitzHugh-Nagumo network under
 Euler-Maruyama and Milstein, the ODE path (fourth-order Runge-Kutta), the
-paper's own speed protocol in FP64, and the CPU oracle timed on this host's
-cores on a bounded sample.
+paper's own speed and accuracy protocols in FP64, and the CPU oracle timed
+on this host's cores on a bounded sample.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -356,10 +356,11 @@ def run_ours(args):
     if not args.no_rk4:
         rk4 = _time_rk4(stream, rank)
 
-    # ---- the paper's own speed protocol (Sec. 2.2.1), FP64 -----------------
-    paper = None
+    # ---- the paper's own speed and accuracy protocols (Sec. 2.2.1, 2.3.1) ----
+    paper, paper_acc = None, None
     if not args.no_paper_protocol:
         paper = _time_paper_protocol(stream, rank)
+        paper_acc = _paper_accuracy_protocol(stream, rank)
 
     # ---- batched heterogeneous instances (one persistent graph launch) -----
     batched = None
@@ -394,7 +395,7 @@ def run_ours(args):
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
             "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "fhn": fhn, "rk4": rk4,
-            "paper_speed_protocol": paper, "cpu_baseline": cpu,
+            "paper_speed_protocol": paper, "paper_accuracy_protocol": paper_acc, "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
         }
@@ -535,6 +536,43 @@ def _time_paper_protocol(stream, rank):
         out["runs"][str(n)] = {"device_s": dev_s, "e2e_s": e2e_s,
                                "orbit_steps_per_sec": orbits * steps / dev_s,
                                "e2e_orbit_steps_per_sec": orbits * steps / e2e_s}
+    return out
+
+
+def _paper_accuracy_protocol(stream, rank):
+    """The paper's accuracy protocol (Sec. 2.3.1): N = 100, 64 realisations,
+    omega ~ U(0.2, 0.4), theta(0) ~ U(-pi, pi), p ~ U(0.01, 0.03),
+    K = 0.02 and 0.2, 400 s, dt = 2^(l-5)/5 for l = 1..5, FP64: the mean and
+    standard deviation over realisations of the coherence r(t_MAX) (Eq. 7)
+    and the device time of each run."""
+    import numpy as np
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    n, orbits = 100, 64
+    out = {"workload": "paper accuracy protocol: Kuramoto paper layout, N = 100, 64 realisations, 400 s, fp64",
+           "runs": []}
+    for K in (0.02, 0.2):
+        p, x0 = inputs.kuramoto_paper_accuracy(K, orbits=orbits, n=n, seed=1 + rank)
+        pd, xd = torch.tensor(p).cuda(), torch.tensor(x0).cuda()
+        for l in range(1, 6):
+            dt = 2.0 ** (l - 5) / 5
+            steps = int(round(400 / dt))
+            pb = sdeb.Problem.make("kuramoto_paper", n, orbits, dt, steps, steps, 0, "fp64")
+            with Integrator(pb) as it:
+                it.set_params(pd, xd, stream=stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                it.integrate(stream=stream)
+                b.record(stream)
+                fin = it.final(stream=stream)
+                torch.cuda.synchronize()
+                r = np.abs(np.exp(1j * fin.cpu().numpy()).mean(axis=1))
+            out["runs"].append({"K": K, "dt": dt, "r_mean": float(r.mean()), "r_sd": float(r.std()),
+                                "device_ms": a.elapsed_time(b)})
     return out
 
 
