@@ -85,7 +85,12 @@ enum {
     /* Geometric Brownian motion dX_i = mu X_i dt + sigma X_i dW_i, m = n, p = (mu, sigma). */
     SDEB_GBM = 5,
     /* Linear ODE (g = 0) dx_i = -theta x_i dt, m = 0, p = (theta). */
-    SDEB_LINEAR_ODE = 6
+    SDEB_LINEAR_ODE = 6,
+    /* A model whose drift and diffusion the caller supplies as CUDA C++
+     * source, compiled at run time for this GPU (sdeb_create_user): n, m and
+     * d are the caller's (1 <= n <= SDEB_USER_MAX_N, 0 <= m <= SDEB_USER_MAX_M,
+     * d >= 0) and the diffusion is a dense n x m matrix. */
+    SDEB_USER = 7
 };
 
 /* Precision.  FP32_KAHAN: float state with a Kahan compensation word per
@@ -120,7 +125,7 @@ enum {
 };
 
 typedef struct {
-    int32_t model;        /* SDEB_KURAMOTO ... SDEB_LINEAR_ODE */
+    int32_t model;        /* SDEB_KURAMOTO ... SDEB_USER */
     int32_t n, m, d;      /* states, Wiener processes, parameters (must match the model) */
     int64_t orbits;       /* orbits in this context, >= 1 */
     double t0, dt;        /* initial time; step > 0 and finite */
@@ -202,6 +207,36 @@ SDEB_API sdeb_status sdeb_batch_layout(const sdeb_ctx *ctx, int32_t instance, in
 SDEB_API sdeb_status sdeb_batch_plan(const sdeb_problem *pbs, int32_t count, double chain_fraction, int32_t num_sms,
                                      int32_t *lanes, int32_t *units_per_lane, int64_t total_orbits,
                                      int32_t *item_task, int32_t *item_slot, int32_t *item_lane0, int32_t *ntasks);
+
+/* Limits of a user-defined model (one GPU thread integrates one orbit and
+ * holds its state, drift and diffusion). */
+#define SDEB_USER_MAX_N 64
+#define SDEB_USER_MAX_M 64
+
+/* A context for a user-defined model (pb->model = SDEB_USER), the GPU
+ * counterpart of the paper's run-time assembly of the OpenCL kernel from
+ * the user's model functions (Sec. 2.1.3, Table 1).  `source` is CUDA C++
+ * (no host headers) defining, for one orbit,
+ *     __device__ void sdeb_drift(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *f);
+ *     __device__ void sdeb_diffusion(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *g);
+ * where sdeb_real is float (SDEB_FP32_KAHAN) or double (SDEB_FP64), x[n] is
+ * the state, p[d] the orbit's parameters, f[n] the drift and g[n * m] the
+ * diffusion, row-major (g[i * m + j]); the macros SDEB_N, SDEB_M and SDEB_D
+ * hold n, m and d.  The library compiles it with NVRTC for the current GPU
+ * (sm_103a) together with its own step kernel: Eq. 2 with the dense
+ * diffusion, X_i += f_i dt + sum_j g_ij sqrt(dt) N_j, f and g at the old
+ * state and t_k = t0 + k dt, the same Philox noise and Box-Muller as the
+ * built-in models, Kahan-compensated FP32 or FP64; with SDEB_FLAG_RK4 the
+ * fourth-order Runge-Kutta step on the drift (sdeb_diffusion is then not
+ * called but must still be defined).  One GPU thread per orbit.  The
+ * context then works as one from sdeb_create (set_params, integrate,
+ * integrate_range, read_orbits, read_final, orbit_flags); sdeb_set_layout,
+ * sdeb_grad and SDEB_FLAG_MILSTEIN return EUNSUPPORTED, ckpt_every must be
+ * 0, sdeb_autotune does nothing.  EINVAL with the compiler's log in
+ * sdeb_last_error(NULL) when the source does not compile; EUNSUPPORTED when
+ * the run-time compiler library (libnvrtc) cannot be loaded; ECUDA when the
+ * compiled kernel cannot be loaded on the device. */
+SDEB_API sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source, sdeb_ctx **out);
 
 /* Free the context and its device buffers (synchronises the device first).
  * NULL is accepted. */

@@ -19,6 +19,7 @@ __all__ = [
     "SDEB_OK", "SDEB_EINVAL", "SDEB_ENOMEM", "SDEB_ECUDA", "SDEB_ETIMEOUT", "SDEB_ESTATE",
     "SDEB_EUNSUPPORTED", "SDEB_ENONFINITE",
     "SDEB_KURAMOTO", "SDEB_KURAMOTO_PAPER", "SDEB_FHN_NET", "SDEB_OU", "SDEB_GBM", "SDEB_LINEAR_ODE",
+    "SDEB_USER", "SDEB_USER_MAX_N", "SDEB_USER_MAX_M", "sdeb_create_user",
     "SDEB_FP32_KAHAN", "SDEB_FP64", "SDEB_FLAG_SHARED_PARAMS", "SDEB_FLAG_NO_FRAMES", "SDEB_FLAG_MILSTEIN",
     "SDEB_FLAG_RK4",
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
@@ -30,13 +31,14 @@ __all__ = [
 ]
 
 SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
-SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER, SDEB_FHN_NET, SDEB_OU, SDEB_GBM, SDEB_LINEAR_ODE = range(1, 7)
+SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER, SDEB_FHN_NET, SDEB_OU, SDEB_GBM, SDEB_LINEAR_ODE, SDEB_USER = range(1, 8)
+SDEB_USER_MAX_N = SDEB_USER_MAX_M = 64
 SDEB_FP32_KAHAN, SDEB_FP64 = 0, 1
 SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES, SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4 = 1, 2, 4, 8
 
 MODEL_IDS = {
     "kuramoto": SDEB_KURAMOTO, "kuramoto_paper": SDEB_KURAMOTO_PAPER, "fhn_net": SDEB_FHN_NET,
-    "ou": SDEB_OU, "gbm": SDEB_GBM, "linear_ode": SDEB_LINEAR_ODE,
+    "ou": SDEB_OU, "gbm": SDEB_GBM, "linear_ode": SDEB_LINEAR_ODE, "user": SDEB_USER,
 }
 PRECISIONS = {"fp32": SDEB_FP32_KAHAN, "fp64": SDEB_FP64}
 
@@ -64,7 +66,12 @@ class Problem(ctypes.Structure):
     def make(cls, model, n, orbits, dt, steps, stride=1, seed=0, precision="fp32", t0=0.0, ckpt_every=0,
              shared_params=False, no_frames=False, orbit_offset=0, m=None, d=None, milstein=False, rk4=False):
         mid = MODEL_IDS.get(model, model)
-        m0, d0 = model_shape(mid, n) if mid in MODEL_IDS.values() else (0, 0)
+        if mid == SDEB_USER:
+            if m is None or d is None:
+                raise ValueError("a user-defined model needs m and d")
+            m0, d0 = m, d
+        else:
+            m0, d0 = model_shape(mid, n) if mid in MODEL_IDS.values() else (0, 0)
         flags = (SDEB_FLAG_SHARED_PARAMS if shared_params else 0) | (SDEB_FLAG_NO_FRAMES if no_frames else 0) | \
             (SDEB_FLAG_MILSTEIN if milstein else 0) | (SDEB_FLAG_RK4 if rk4 else 0)
         return cls(mid, n, m0 if m is None else m, d0 if d is None else d, orbits, t0, dt, steps, stride,
@@ -106,6 +113,7 @@ _SIGS = {
     "sdeb_get_layout": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sdeb_autotune": (_ST, [_P, ctypes.c_int64, _P]),
     "sdeb_create_batch": (_ST, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "sdeb_create_user": (_ST, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
     "sdeb_batch_read": (_ST, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.c_int32, _P]),
     "sdeb_batch_info": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_int32)]),
@@ -203,6 +211,15 @@ def sdeb_set_layout(ctx, lanes_per_orbit, units_per_lane):
 
 def sdeb_autotune(ctx, trial_steps=0, stream=None):
     _check(lib().sdeb_autotune(ctx, trial_steps, _stream(stream)), ctx)
+
+
+def sdeb_create_user(problem, source):
+    """Context for a user-defined model (problem.model = SDEB_USER): `source`
+    defines sdeb_drift and sdeb_diffusion in CUDA C++ (include/sdeb.h)."""
+    ctx = _P()
+    _check(lib().sdeb_create_user(ctypes.byref(problem), source.encode() if isinstance(source, str) else source,
+                                  ctypes.byref(ctx)))
+    return ctx
 
 
 def sdeb_create_batch(problems):

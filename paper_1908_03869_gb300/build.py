@@ -20,9 +20,34 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libsdeb.so"
 LIB_PATH = os.path.join(BUILD_DIR, LIB_NAME)
 
+GEN_DIR = os.path.join(BUILD_DIR, "gen")
+
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "-I" + INCLUDE, "-I" + CSRC]
+              "-I" + INCLUDE, "-I" + CSRC, "-I" + GEN_DIR]
+
+# Device sources compiled again at run time for user-defined models (NVRTC):
+# embedded into the library as string constants, one per file.
+RTC_EMBED = [("kRtcEmDevice", "em_device.cuh"), ("kRtcArgs", "rtc_args.h"), ("kRtcKernel", "rtc_kernel.cuh")]
+RTC_INC = os.path.join(GEN_DIR, "sdeb_rtc_sources.inc")
+
+
+def generate_rtc_sources():
+    parts = ["// Generated by build.py from csrc/: the device sources of the run-time compiled kernel.\n"]
+    for name, fname in RTC_EMBED:
+        with open(os.path.join(CSRC, fname)) as f:
+            text = f.read()
+        if ")SDEBRTC" in text:
+            raise RuntimeError("%s contains the raw-string delimiter" % fname)
+        parts.append('static const char %s[] = R"SDEBRTC(%s)SDEBRTC";\n' % (name, text))
+    content = "".join(parts)
+    os.makedirs(GEN_DIR, exist_ok=True)
+    if os.path.exists(RTC_INC):
+        with open(RTC_INC) as f:
+            if f.read() == content:
+                return
+    with open(RTC_INC, "w") as f:
+        f.write(content)
 
 
 def _nvcc():
@@ -63,6 +88,7 @@ def build(force=False, verbose_ptxas=False, jobs=None):
     if not force and not needs_build():
         return LIB_PATH
     os.makedirs(BUILD_DIR, exist_ok=True)
+    generate_rtc_sources()
     srcs = sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as ex:
@@ -71,7 +97,7 @@ def build(force=False, verbose_ptxas=False, jobs=None):
         for _, log in results:
             sys.stderr.write(log)
     tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-cudart", "static"]
+    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-cudart", "static", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)

@@ -12,8 +12,17 @@
 //   * Butterfly sums over the G lanes that share an orbit.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Compiled at run time (NVRTC) for user-defined models: no host headers.
+typedef unsigned char uint8_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+#else
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 namespace sdeb {
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "em_internal.h"
+#include "sdeb_rtc.h"
 #include "sdeb.h"
 
 using namespace sdeb;
@@ -36,6 +37,7 @@ struct sdeb_ctx {
     bool params_set = false;
     int64_t k_current = 0;
     std::string err;
+    RtcModule *rtc = nullptr;             // user-defined model: its run-time compiled kernel
     // ---- batch contexts (sdeb_create_batch) ----
     bool is_batch = false;
     std::vector<sdeb_problem> probs;
@@ -126,13 +128,25 @@ void free_buffers(sdeb_ctx *c) {
     c->d_params = c->d_x = c->d_frames = c->d_ckpt = nullptr;
     c->d_comp = c->d_ckpt_comp = nullptr;
     c->d_flags = nullptr;
+    rtc_release(c->rtc);
+    c->rtc = nullptr;
 }
 
 sdeb_status validate(const sdeb_problem *pb, int32_t &units) {
     if (!pb) return fail(nullptr, SDEB_EINVAL, "problem is NULL");
     int32_t m = 0, d = 0;
     if (pb->n <= 0) return fail(nullptr, SDEB_EINVAL, "n must be positive (got %d)", pb->n);
-    if (!model_shape(pb->model, pb->n, m, d, units))
+    if (pb->model == SDEB_USER) {
+        if (pb->n > SDEB_USER_MAX_N || pb->m < 0 || pb->m > SDEB_USER_MAX_M || pb->d < 0)
+            return fail(nullptr, SDEB_EINVAL, "a user model needs 1 <= n <= %d, 0 <= m <= %d, d >= 0",
+                        SDEB_USER_MAX_N, SDEB_USER_MAX_M);
+        if (pb->flags & SDEB_FLAG_MILSTEIN)
+            return fail(nullptr, SDEB_EUNSUPPORTED, "user models integrate by Euler-Maruyama or SDEB_FLAG_RK4");
+        if (pb->ckpt_every != 0) return fail(nullptr, SDEB_EUNSUPPORTED, "user models keep no checkpoints");
+        m = pb->m;
+        d = pb->d;
+        units = pb->n;
+    } else if (!model_shape(pb->model, pb->n, m, d, units))
         return fail(nullptr, SDEB_EINVAL, "unknown model %d or n=%d invalid for it", pb->model, pb->n);
     if (pb->m != m || pb->d != d)
         return fail(nullptr, SDEB_EINVAL, "model %d with n=%d needs m=%d d=%d (got m=%d d=%d)", pb->model,
@@ -543,6 +557,8 @@ sdeb_status build_batch_instances(const sdeb_problem *pbs, int32_t count, std::v
     return SDEB_OK;
 }
 
+sdeb_status create_context(const sdeb_problem *pb, int32_t units, sdeb_ctx **out);
+
 }  // namespace
 
 namespace sdeb {
@@ -576,7 +592,39 @@ sdeb_status sdeb_create(const sdeb_problem *pb, sdeb_ctx **out) {
     int32_t units = 0;
     sdeb_status st = validate(pb, units);
     if (st != SDEB_OK) return st;
+    if (pb->model == SDEB_USER)
+        return fail(nullptr, SDEB_EINVAL, "a user-defined model needs its source: use sdeb_create_user");
+    return create_context(pb, units, out);
+}
 
+sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source, sdeb_ctx **out) {
+    if (!out) return fail(nullptr, SDEB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!source) return fail(nullptr, SDEB_EINVAL, "source is NULL");
+    int32_t units = 0;
+    sdeb_status st = validate(pb, units);
+    if (st != SDEB_OK) return st;
+    if (pb->model != SDEB_USER) return fail(nullptr, SDEB_EINVAL, "sdeb_create_user needs model SDEB_USER");
+    RtcModule *m = nullptr;
+    std::string log;
+    st = rtc_build(*pb, source, &m, log);
+    if (st != SDEB_OK) return fail(nullptr, st, "user model: %s", log.c_str());
+    sdeb_ctx *c = nullptr;
+    st = create_context(pb, units, &c);
+    if (st != SDEB_OK) {
+        rtc_release(m);
+        return st;
+    }
+    c->rtc = m;
+    *out = c;
+    return SDEB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+sdeb_status create_context(const sdeb_problem *pb, int32_t units, sdeb_ctx **out) {
     const size_t elem = pb->precision == SDEB_FP64 ? 8 : 4;
     const bool shared = pb->flags & SDEB_FLAG_SHARED_PARAMS;
     int64_t state_elems, param_elems, frame_elems = 0, ckpt_elems = 0, seg_elems = 0, gradp_elems = 0;
@@ -634,6 +682,10 @@ sdeb_status sdeb_create(const sdeb_problem *pb, sdeb_ctx **out) {
     *out = c;
     return SDEB_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 void sdeb_destroy(sdeb_ctx *ctx) {
     if (!ctx) return;
@@ -700,6 +752,27 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
     if (k_end < k_begin || k_end > ctx->pb.steps)
         return fail(ctx, SDEB_EINVAL, "k_end=%lld outside [k_begin, steps]", (long long)k_end);
     if (k_end == k_begin) return SDEB_OK;
+    if (ctx->rtc) {
+        UserArgs u{};
+        u.params = ctx->d_params;
+        u.param_stride = (ctx->pb.flags & SDEB_FLAG_SHARED_PARAMS) ? 0 : ctx->pb.d;
+        u.x = ctx->d_x;
+        u.comp = ctx->d_comp;
+        u.frames = ctx->d_frames;
+        u.orbits = ctx->pb.orbits;
+        u.t0 = ctx->pb.t0;
+        u.dt = ctx->pb.dt;
+        u.k_begin = (uint32_t)k_begin;
+        u.k_end = (uint32_t)k_end;
+        u.stride = (uint32_t)ctx->pb.stride;
+        u.orbit_offset = (uint32_t)ctx->pb.orbit_offset;
+        u.flags = ctx->d_flags;
+        u.keys = philox_key_schedule(ctx->pb.seed);
+        cudaError_t e = rtc_launch(ctx->rtc, u, as_stream(stream));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "user model kernel launch");
+        ctx->k_current = k_end;
+        return SDEB_OK;
+    }
     ForwardArgs a{};
     a.model = ctx->pb.model;
     a.n = ctx->pb.n;
@@ -804,6 +877,7 @@ sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream) {
 sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int32_t units_per_lane) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "a batch chooses layouts per instance (sdeb_autotune)");
+    if (ctx->rtc) return fail(ctx, SDEB_EUNSUPPORTED, "a user model runs one thread per orbit");
     const int G = lanes_per_orbit, P = units_per_lane;
     if (!(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32) || P < 1 || P > 16 ||
         (G > 1 && P % 4 != 0) || (int64_t)G * P < ctx->units)
@@ -821,6 +895,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
     if (ctx->is_batch) return autotune_batch(ctx, as_stream(stream));
     if (!ctx->params_set || ctx->k_current != 0)
         return fail(ctx, SDEB_ESTATE, "call sdeb_autotune after sdeb_set_params and before integrating");
+    if (ctx->rtc) return SDEB_OK;  // a user model has one kernel shape: one thread per orbit
     // A context that keeps checkpoints for sdeb_grad is tuned for forward +
     // adjoint: both are timed over one segment (at most 1024 steps) from
     // checkpoint 0, which sdeb_set_params has written.

@@ -20,13 +20,20 @@ def _ptr(t):
 class Integrator:
     """Owns one sdeb context.  ``Integrator(Problem.make(...))``."""
 
-    def __init__(self, problem: Problem):
+    def __init__(self, problem: Problem, user_source=None):
+        """user_source: CUDA C++ of a user-defined model (problem.model =
+        SDEB_USER), compiled at run time (sdeb_create_user)."""
         self.pb = problem
         self.dtype = torch.float64 if problem.precision == SDEB_FP64 else torch.float32
         self.shared = bool(problem.flags & SDEB_FLAG_SHARED_PARAMS)
         self.has_frames = not (problem.flags & SDEB_FLAG_NO_FRAMES)
         self.nframes = problem.steps // problem.stride + 1 if self.has_frames else 0
-        self.ctx = sdeb_create(problem)
+        self.ctx = None
+        if user_source is not None:
+            from . import sdeb_create_user
+            self.ctx = sdeb_create_user(problem, user_source)
+        else:
+            self.ctx = sdeb_create(problem)
 
     def close(self):
         if self.ctx is not None:
