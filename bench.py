@@ -14,9 +14,10 @@ for the dominant kernel (the forward Euler-Maruyama kernel, bound by the
 SFU / special-function pipe), the same workload in FP64 on a 1000-step
 prefix of the horizon, the discrete adjoint against its forward, the
 batched heterogeneous workload, the FitzHugh-Nagumo network under
-Euler-Maruyama and Milstein, the ODE path (fourth-order Runge-Kutta), the
-paper's own speed and accuracy protocols in FP64, and the CPU oracle timed
-on this host's cores on a bounded sample.
+Euler-Maruyama and Milstein, the ODE path (fourth-order Runge-Kutta), a
+user-defined model compiled at run time, the paper's own speed and accuracy
+protocols in FP64, and the CPU oracle timed on this host's cores on a
+bounded sample.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -356,6 +357,11 @@ def run_ours(args):
     if not args.no_rk4:
         rk4 = _time_rk4(stream, rank)
 
+    # ---- a user-defined model compiled at run time, beside the built-in one --
+    user = None
+    if not args.no_user_model:
+        user = _time_user_model(stream, rank)
+
     # ---- the paper's own speed and accuracy protocols (Sec. 2.2.1, 2.3.1) ----
     paper, paper_acc = None, None
     if not args.no_paper_protocol:
@@ -395,7 +401,8 @@ def run_ours(args):
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
             "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "fhn": fhn, "rk4": rk4,
-            "paper_speed_protocol": paper, "paper_accuracy_protocol": paper_acc, "cpu_baseline": cpu,
+            "user_model": user, "paper_speed_protocol": paper, "paper_accuracy_protocol": paper_acc,
+            "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
         }
@@ -481,6 +488,70 @@ def _time_fhn(stream, rank, reps=3, steps=10000):
     peak = SFU_PER_SM_PER_CLK * NUM_SMS * SM_MAX_MHZ * 1e6
     # one normal per unit-step: half of (log2, sqrt, sin, cos) = 2 SFU operations
     out["sfu_roofline_frac_em"] = 2.0 * out["euler_maruyama"]["unit_steps_per_sec"] / peak
+    return out
+
+
+# A FitzHugh-Nagumo network written as a user-defined model (the run-time
+# compiled path, diagonal-noise form; x = (v_1..v_u, w_1..w_u),
+# p = (a, b, eps, I, c, sigma)).
+USER_FHN_SOURCE = r"""
+#define SDEB_DIAGONAL_NOISE 1
+__device__ void sdeb_drift(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *f) {
+    const int u = SDEB_N / 2;
+    sdeb_real mean = 0;
+    for (int i = 0; i < u; ++i) mean += x[i];
+    mean /= u;
+    for (int i = 0; i < u; ++i) {
+        const sdeb_real v = x[i], w = x[u + i];
+        f[i] = v - v * v * v / 3 - w + p[3] + p[4] * mean - p[4] * v;
+        f[u + i] = p[2] * (v + p[0] - p[1] * w);
+    }
+}
+__device__ void sdeb_diffusion(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *g) {
+    for (int j = 0; j < SDEB_M; ++j) g[j] = p[5] * x[j];
+}
+"""
+
+
+def _time_user_model(stream, rank, reps=3, steps=1000):
+    """A FitzHugh-Nagumo network of 16 units (n = 32) on 2^18 orbits, dt =
+    0.01, 1000 steps, FP32: compile time of the run-time compiled user model
+    and its unit-steps/s beside the built-in model's."""
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.integrator import Integrator
+    from paper_1908_03869_gb300.sharding import weak_scaling_offset
+
+    n, orbits = 32, 1 << 18
+    p, x0 = inputs.fhn(n // 2, orbits, seed=1 + rank)
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    xt = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    out = {"workload": "FitzHugh-Nagumo network, 16 units (n = 32), 2^18 orbits, dt = 0.01, %d steps, fp32"
+                       % steps}
+    for name in ("built_in", "user_source"):
+        user = name == "user_source"
+        pb = sdeb.Problem.make("user" if user else "fhn_net", n, orbits, 0.01, steps, 100, 0, "fp32",
+                               orbit_offset=weak_scaling_offset(orbits, rank), m=n // 2, d=6)
+        t0 = time.perf_counter()
+        it = Integrator(pb, user_source=USER_FHN_SOURCE if user else None)
+        create_s = time.perf_counter() - t0
+        times = []
+        try:
+            for _ in range(reps + 1):
+                it.set_params(pt, xt, stream=stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                it.integrate(stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+        finally:
+            it.close()
+        ms = statistics.median(times[1:])
+        out[name] = {"create_s": create_s, "ms": ms, "unit_steps_per_sec": orbits * (n // 2) * steps / (ms / 1e3)}
+    out["user_time_over_built_in"] = out["user_source"]["ms"] / out["built_in"]["ms"]
     return out
 
 
@@ -693,6 +764,7 @@ def main():
     ap.add_argument("--no-fhn", action="store_true")
     ap.add_argument("--no-rk4", action="store_true")
     ap.add_argument("--no-paper-protocol", action="store_true")
+    ap.add_argument("--no-user-model", action="store_true")
     ap.add_argument("--orbit-scale", type=float, default=1.0,
                     help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
     ap.add_argument("--horizon", type=int, default=None,

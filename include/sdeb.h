@@ -222,7 +222,9 @@ SDEB_API sdeb_status sdeb_batch_plan(const sdeb_problem *pbs, int32_t count, dou
  * where sdeb_real is float (SDEB_FP32_KAHAN) or double (SDEB_FP64), x[n] is
  * the state, p[d] the orbit's parameters, f[n] the drift and g[n * m] the
  * diffusion, row-major (g[i * m + j]); the macros SDEB_N, SDEB_M and SDEB_D
- * hold n, m and d.  The library compiles it with NVRTC for the current GPU
+ * hold n, m and d.  A source that defines SDEB_DIAGONAL_NOISE (before its
+ * functions) gives only g[m]: channel j drives state component j alone with
+ * g_jj = g[j], the O(n) form.  The library compiles it with NVRTC for the current GPU
  * (sm_103a) together with its own step kernel: Eq. 2 with the dense
  * diffusion, X_i += f_i dt + sum_j g_ij sqrt(dt) N_j, f and g at the old
  * state and t_k = t0 + k dt, the same Philox noise and Box-Muller as the

@@ -7,7 +7,9 @@
 // provides, for one orbit,
 //   __device__ void sdeb_drift(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *f);
 //   __device__ void sdeb_diffusion(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *g);
-// with f[SDEB_N] and g[SDEB_N * SDEB_M] (row-major, g[i * SDEB_M + j]).
+// with f[SDEB_N] and g[SDEB_N * SDEB_M] (row-major, g[i * SDEB_M + j]); or, if
+// the user's code defines SDEB_DIAGONAL_NOISE, g[SDEB_M] with channel j
+// driving state component j alone (g[j] = g_jj), the O(n) form.
 //
 // One thread integrates one orbit: Eq. 2 with the dense diffusion,
 // X_i += f_i dt + sum_j g_ij sqrt(dt) N_j, f and g at the old state and
@@ -28,6 +30,7 @@ extern "C" __global__ void sdeb_user_kernel(const UserArgs a) {
     const sdeb_real *p = static_cast<const sdeb_real *>(a.params) + o * a.param_stride;
     sdeb_real *xrow = static_cast<sdeb_real *>(a.x) + o * SDEB_N;
     sdeb_real x[SDEB_N], c[SDEB_N], f[SDEB_N];
+#pragma unroll
     for (int i = 0; i < SDEB_N; ++i) {
         x[i] = xrow[i];
         c[i] = kKahan ? (sdeb_real)a.comp[o * SDEB_N + i] : sdeb_real(0);
@@ -60,28 +63,42 @@ extern "C" __global__ void sdeb_user_kernel(const UserArgs a) {
 #else
         sdeb_drift(t, x, p, f);
 #if SDEB_M > 0
-        sdeb_real g[SDEB_N * SDEB_M], z[(SDEB_M + 3) / 4 * 4];
+#ifdef SDEB_DIAGONAL_NOISE
+        sdeb_real g[SDEB_M];
+#else
+        sdeb_real g[SDEB_N * SDEB_M];
+#endif
+        sdeb_real z[(SDEB_M + 3) / 4 * 4];
         sdeb_diffusion(t, x, p, g);
+#pragma unroll
         for (int b = 0; b < (SDEB_M + 3) / 4; ++b) {
             const U32x4 w = philox4x32_10(k, (uint32_t)b, gorb, 0u, a.keys);
             box_muller<sdeb_real>(w.x, w.y, z[4 * b], z[4 * b + 1]);
             box_muller<sdeb_real>(w.z, w.w, z[4 * b + 2], z[4 * b + 3]);
         }
 #endif
+#pragma unroll
         for (int i = 0; i < SDEB_N; ++i) {
             sdeb_real noise = 0;
 #if SDEB_M > 0
+#ifdef SDEB_DIAGONAL_NOISE
+            if (i < SDEB_M) noise = g[i] * sqdt * z[i];
+#else
+#pragma unroll
             for (int j = 0; j < SDEB_M; ++j) noise += g[i * SDEB_M + j] * sqdt * z[j];
+#endif
 #endif
             rtc_accumulate(x[i], c[i], f[i] * dt + noise);
         }
 #endif
         if (frames != nullptr && (k + 1) % a.stride == 0) {
             sdeb_real *fr = frames + ((long long)((k + 1) / a.stride) * a.orbits + o) * SDEB_N;
+#pragma unroll
             for (int i = 0; i < SDEB_N; ++i) fr[i] = x[i];
         }
     }
     bool bad = false;
+#pragma unroll
     for (int i = 0; i < SDEB_N; ++i) {
         xrow[i] = x[i];
         if (kKahan) a.comp[o * SDEB_N + i] = (float)c[i];

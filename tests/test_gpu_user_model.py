@@ -4,8 +4,9 @@ counterpart of the paper's run-time assembly of the OpenCL source,
 Sec. 2.1.3).
 
 * Sources restating GBM, Kuramoto (pairwise, Eq. 6) and the FitzHugh-Nagumo
-  network against the oracle's built-in models on the same inputs and
-  noise: FP64 <= 1e-12, FP32 <= 1e-4 (frames and final state).
+  network (dense and diagonal noise forms) against the oracle's built-in
+  models on the same inputs and noise: FP64 <= 1e-12, FP32 <= 1e-4 (frames
+  and final state).
 * Dense noise (a 2-state linear SDE driven by 3 Wiener channels) against
   Euler-Maruyama written out in numpy on the oracle's normals: FP64 1e-12.
 * The ODE path (SDEB_FLAG_RK4) on the Kuramoto source against the oracle's
@@ -59,7 +60,7 @@ def _cast(precision, *arrays):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["gbm", "kuramoto", "fhn_net"])
+@pytest.mark.parametrize("name", ["gbm", "kuramoto", "fhn_net", "fhn_net_diagonal"])
 def test_user_sources_match_the_oracle_models(precision, name):
     orbits, steps, stride, dt = 160, 300, 50, 0.01
     if name == "gbm":
@@ -69,7 +70,9 @@ def test_user_sources_match_the_oracle_models(precision, name):
         n, src = 8, user_models.KURAMOTO_PAIRWISE
         p, x0 = inputs.kuramoto(n, orbits, seed=42)
     else:
-        n, src = 16, user_models.FHN
+        n = 16
+        src = user_models.FHN if name == "fhn_net" else user_models.FHN_DIAGONAL
+        name = "fhn_net"
         p, x0 = inputs.fhn(n // 2, orbits, seed=43)
     m, d = sdeb.model_shape(name, n)
     p, x0 = _cast(precision, p, x0)

@@ -65,3 +65,22 @@ __device__ void sdeb_drift(double t, const sdeb_real *x, const sdeb_real *p, sde
 }
 __device__ void sdeb_diffusion(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *g) {}
 """
+
+# The same network with the diagonal-noise form: g[j] drives v_j.
+FHN_DIAGONAL = r"""
+#define SDEB_DIAGONAL_NOISE 1
+__device__ void sdeb_drift(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *f) {
+    const int u = SDEB_N / 2;
+    sdeb_real mean = 0;
+    for (int i = 0; i < u; ++i) mean += x[i];
+    mean /= u;
+    for (int i = 0; i < u; ++i) {
+        const sdeb_real v = x[i], w = x[u + i];
+        f[i] = v - v * v * v / 3 - w + p[3] + p[4] * mean - p[4] * v;
+        f[u + i] = p[2] * (v + p[0] - p[1] * w);
+    }
+}
+__device__ void sdeb_diffusion(double t, const sdeb_real *x, const sdeb_real *p, sdeb_real *g) {
+    for (int j = 0; j < SDEB_M; ++j) g[j] = p[5] * x[j];
+}
+"""
