@@ -49,6 +49,9 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
     M model;
     model.load(prow, u0, units, dt, sqdt);
     const Real kdt_n = mul_r(model.kn, dt);
+    Real kdt_n_live[P];  // (K/n) dt for the orbit's units, 0 for padding
+#pragma unroll
+    for (int i = 0; i < P; ++i) kdt_n_live[i] = kdt_n * model.live[i];
     const uint32_t gorb = a.orbit_offset + (uint32_t)o;
 
     Real lam[1][P];
@@ -109,17 +112,18 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
                 load_units<Real, 1, P>(row, units, u0, rn);
                 load_units<Real, 1, P>(row + n, units, u0, zn);
             }
+            // Padding units: live = 0 keeps them out of C and S, and their
+            // lambda stays 0 (it starts at 0 and its update is scaled by
+            // live), so they add nothing to A, B or the gradients.
             Real sn[P], cs[P];
             Real C = 0, S = 0, A = 0, B = 0;
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 sincos_reduced(r[0][i], sn[i], cs[i]);
-                if (u0 + i < units) {
-                    C += cs[i];
-                    S += sn[i];
-                    A = fma_r(lam[0][i], cs[i], A);
-                    B = fma_r(lam[0][i], sn[i], B);
-                }
+                C = fma_r(model.live[i], cs[i], C);
+                S = fma_r(model.live[i], sn[i], S);
+                A = fma_r(lam[0][i], cs[i], A);
+                B = fma_r(lam[0][i], sn[i], B);
             }
             C = group_sum<G>(C);
             S = group_sum<G>(S);
@@ -127,16 +131,14 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             B = group_sum<G>(B);
 #pragma unroll
             for (int i = 0; i < P; ++i) {
-                if (u0 + i < units) {
-                    const Real l = lam[0][i];
-                    // parameter gradients use lambda^{k+1}
-                    g_k = fma_r(l, fma_r(S, cs[i], -mul_r(C, sn[i])), g_k);
-                    g_omega[i] += l;
-                    g_noise[PAPER ? i : 0] = fma_r(l, z[0][i], g_noise[PAPER ? i : 0]);
-                    // lambda^k
-                    const Real jac = fma_r(cs[i], A, mul_r(sn[i], B)) - l * fma_r(cs[i], C, mul_r(sn[i], S));
-                    lam[0][i] = fma_r(kdt_n, jac, l);
-                }
+                const Real l = lam[0][i];
+                // parameter gradients use lambda^{k+1}
+                g_k = fma_r(l, fma_r(S, cs[i], -mul_r(C, sn[i])), g_k);
+                g_omega[i] += l;
+                g_noise[PAPER ? i : 0] = fma_r(l, z[0][i], g_noise[PAPER ? i : 0]);
+                // lambda^k
+                const Real jac = fma_r(cs[i], A, mul_r(sn[i], B)) - l * fma_r(cs[i], C, mul_r(sn[i], S));
+                lam[0][i] = fma_r(kdt_n_live[i], jac, l);
             }
         }
     }

@@ -156,7 +156,6 @@ extern "C" sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void
     a.keys = philox_key_schedule(pb->seed);
     a.milstein = (pb->flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     a.rk4 = (pb->flags & SDEB_FLAG_RK4) ? 1 : 0;
-    const bool phase = pb->model == SDEB_KURAMOTO || pb->model == SDEB_KURAMOTO_PAPER;
     e = launch_forward_any(a, layout, fp64, s);
     if (e == cudaErrorNotSupported) return fail(SDEB_EUNSUPPORTED, "no kernel for this model and layout");
     if (e != cudaSuccess) return fail(SDEB_ECUDA, "forward kernel launch failed");
