@@ -38,6 +38,7 @@ class Problem(ctypes.Structure):
         ("mean_field", ctypes.c_int32),
         ("milstein", ctypes.c_int32),
         ("rk4", ctypes.c_int32),
+        ("implicit", ctypes.c_int32),
     ]
 
 
@@ -66,6 +67,7 @@ def lib():
         L.oracle_drift.argtypes = [ctypes.POINTER(Problem), ctypes.c_double, _P, _P, _P]
         L.oracle_diffusion.argtypes = [ctypes.POINTER(Problem), ctypes.c_double, _P, _P, _P]
         L.oracle_diffusion_diag_derivative.argtypes = [ctypes.POINTER(Problem), ctypes.c_double, _P, _P, _P]
+        L.oracle_drift_jacobian.argtypes = [ctypes.POINTER(Problem), ctypes.c_double, _P, _P, _P]
         L.oracle_check_problem.argtypes = [ctypes.POINTER(Problem)]
         L.oracle_integrate.argtypes = [ctypes.POINTER(Problem), _P, _P, ctypes.c_int64,
                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P,
@@ -81,11 +83,15 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(_P)
 
 
+IMPLICIT = {None: 0, "euler": 1, "midpoint": 2}
+
+
 def make_problem(model, n, m, d, dt, steps, stride=1, seed=0, t0=0.0,
-                 shared_params=False, mean_field=False, milstein=False, rk4=False):
+                 shared_params=False, mean_field=False, milstein=False, rk4=False, implicit=None):
     return Problem(MODELS[model] if isinstance(model, str) else int(model), n, m, d, float(t0),
                    float(dt), int(steps), int(stride), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                   int(bool(shared_params)), int(bool(mean_field)), int(bool(milstein)), int(bool(rk4)))
+                   int(bool(shared_params)), int(bool(mean_field)), int(bool(milstein)), int(bool(rk4)),
+                   IMPLICIT[implicit])
 
 
 def philox(ctr, key):
@@ -141,6 +147,15 @@ def diffusion_diag_derivative(pb, x, p, t=0.0):
     dg = np.zeros(max(pb.m, 1), dtype=np.float64)
     assert lib().oracle_diffusion_diag_derivative(ctypes.byref(pb), t, _ptr(x), _ptr(p), _ptr(dg)) == 0
     return dg[:pb.m]
+
+
+def drift_jacobian(pb, x, p, t=0.0):
+    """J[i][j] = d f_i / d x_j."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    J = np.zeros((pb.n, pb.n), dtype=np.float64)
+    assert lib().oracle_drift_jacobian(ctypes.byref(pb), t, _ptr(x), _ptr(p), _ptr(J)) == 0
+    return J
 
 
 def integrate(pb, params, x0, orbit_begin=0, k_begin=0, k_end=None, frames=True, nthreads=1):

@@ -142,6 +142,8 @@ int oracle_check_problem(const oracle_problem *pb)
     if (pb->milstein != 0 && pb->milstein != 1) return -1;
     if (pb->rk4 != 0 && pb->rk4 != 1) return -1;
     if (pb->milstein && pb->rk4) return -1;
+    if (pb->implicit < 0 || pb->implicit > 2) return -1;
+    if (pb->implicit && (pb->milstein || pb->rk4)) return -1;
     switch (pb->model) {
     case ORACLE_KURAMOTO:       return (m == n && d == n + 2) ? 0 : -1;
     case ORACLE_KURAMOTO_PAPER: return (m == n && d == 2 * n + 1) ? 0 : -1;
@@ -270,12 +272,90 @@ int oracle_diffusion_diag_derivative(const oracle_problem *pb, double t, const d
     }
 }
 
+/* Jacobian of the drift, from the drifts above (Kuramoto by the pairwise
+ * definition: d/dx_l of sum_j sin(x_j - x_i)). */
+int oracle_drift_jacobian(const oracle_problem *pb, double t, const double *x, const double *p, double *J)
+{
+    (void)t;
+    int n = pb->n;
+    for (int i = 0; i < n * n; ++i) J[i] = 0.0;
+    switch (pb->model) {
+    case ORACLE_KURAMOTO:
+    case ORACLE_KURAMOTO_PAPER: {
+        double kn = p[0] / n;
+        for (int i = 0; i < n; ++i) {
+            double diag = 0.0;
+            for (int l = 0; l < n; ++l) {
+                if (l == i) continue;
+                double cl = cos(x[l] - x[i]);
+                J[i * n + l] = kn * cl;
+                diag -= kn * cl;
+            }
+            J[i * n + i] = diag;
+        }
+        return 0;
+    }
+    case ORACLE_FHN_NET: {
+        int u = n / 2;
+        double b = p[1], eps = p[2], c = p[4];
+        for (int i = 0; i < u; ++i) {
+            for (int j = 0; j < u; ++j) J[i * n + j] = c / u;          /* c mean(v) */
+            J[i * n + i] += 1.0 - x[i] * x[i] - c;                     /* v - v^3/3 - c v */
+            J[i * n + u + i] = -1.0;                                    /* - w */
+            J[(u + i) * n + i] = eps;                                   /* eps v */
+            J[(u + i) * n + u + i] = -eps * b;                          /* - eps b w */
+        }
+        return 0;
+    }
+    case ORACLE_OU:
+    case ORACLE_LINEAR_ODE:
+        for (int i = 0; i < n; ++i) J[i * n + i] = -p[0];
+        return 0;
+    case ORACLE_GBM:
+        for (int i = 0; i < n; ++i) J[i * n + i] = p[0];
+        return 0;
+    default:
+        return -1;
+    }
+}
+
+/* Solves A z = r in place (z overwrites r) by Gaussian elimination with
+ * partial pivoting; A (n x n, row-major) is overwritten. */
+static void dense_solve(int n, double *A, double *r)
+{
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < n; ++i)
+            if (fabs(A[i * n + col]) > fabs(A[piv * n + col])) piv = i;
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) {
+                double tmp = A[col * n + j];
+                A[col * n + j] = A[piv * n + j];
+                A[piv * n + j] = tmp;
+            }
+            double tmp = r[col];
+            r[col] = r[piv];
+            r[piv] = tmp;
+        }
+        for (int i = col + 1; i < n; ++i) {
+            double m = A[i * n + col] / A[col * n + col];
+            for (int j = col; j < n; ++j) A[i * n + j] -= m * A[col * n + j];
+            r[i] -= m * r[col];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double acc = r[i];
+        for (int j = i + 1; j < n; ++j) acc -= A[i * n + j] * r[j];
+        r[i] = acc / A[i * n + i];
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Euler-Maruyama, Eq. 2, and the Milstein step.                             */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    double *f, *g, *N, *xn, *dg, *k[4], *y;
+    double *f, *g, *N, *xn, *dg, *k[4], *y, *J;
 } em_scratch;
 
 static int scratch_alloc(em_scratch *s, int n, int m)
@@ -286,7 +366,8 @@ static int scratch_alloc(em_scratch *s, int n, int m)
     s->xn = (double *)malloc(sizeof(double) * (size_t)n);
     s->dg = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     s->y = (double *)malloc(sizeof(double) * (size_t)n);
-    int ok = s->f && s->g && s->N && s->xn && s->dg && s->y;
+    s->J = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    int ok = s->f && s->g && s->N && s->xn && s->dg && s->y && s->J;
     for (int q = 0; q < 4; ++q) {
         s->k[q] = (double *)malloc(sizeof(double) * (size_t)n);
         ok = ok && s->k[q];
@@ -296,7 +377,7 @@ static int scratch_alloc(em_scratch *s, int n, int m)
 
 static void scratch_free(em_scratch *s)
 {
-    free(s->f); free(s->g); free(s->N); free(s->xn); free(s->dg); free(s->y);
+    free(s->f); free(s->g); free(s->N); free(s->xn); free(s->dg); free(s->y); free(s->J);
     for (int q = 0; q < 4; ++q) free(s->k[q]);
 }
 
@@ -323,11 +404,43 @@ static void rk4_step(const oracle_problem *pb, const double *p, int64_t k, doubl
 /* One step of Eq. 2 at step index k (reading of Eq. 2's t: the drift and
  * diffusion of step k are evaluated at t_k = t0 + k dt and at the old state,
  * the update of all components is simultaneous). */
+/* One step of an implicit ODE scheme on the drift alone (the paper lists
+ * implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.2):
+ *   implicit Euler:    y = x + h f(t + h, y),
+ *   implicit midpoint: y = x + h f(t + h/2, (x + y) / 2),
+ * solved by ORACLE_NEWTON_ITERS Newton iterations from y = x on
+ * G(y) = y - x - h f(t + theta h, x + theta (y - x)) (theta = 1 or 1/2),
+ * G'(y) = I - theta h J(x + theta (y - x)), with a dense solve. */
+static void implicit_step(const oracle_problem *pb, const double *p, int64_t k, double *x, em_scratch *s)
+{
+    int n = pb->n;
+    double h = pb->dt, theta = pb->implicit == 1 ? 1.0 : 0.5;
+    double t = pb->t0 + ((double)k + theta) * h;
+    double *y = s->xn, *z = s->y, *r = s->k[0];
+    memcpy(y, x, sizeof(double) * (size_t)n);
+    for (int it = 0; it < ORACLE_NEWTON_ITERS; ++it) {
+        for (int i = 0; i < n; ++i) z[i] = x[i] + theta * (y[i] - x[i]);
+        oracle_drift(pb, t, z, p, s->f);
+        oracle_drift_jacobian(pb, t, z, p, s->J);
+        for (int i = 0; i < n; ++i) {
+            r[i] = -(y[i] - x[i] - h * s->f[i]);
+            for (int j = 0; j < n; ++j) s->J[i * n + j] = (i == j ? 1.0 : 0.0) - theta * h * s->J[i * n + j];
+        }
+        dense_solve(n, s->J, r);
+        for (int i = 0; i < n; ++i) y[i] += r[i];
+    }
+    memcpy(x, y, sizeof(double) * (size_t)n);
+}
+
 static void em_step(const oracle_problem *pb, const double *p, int64_t k, uint32_t orbit,
                     double *x, em_scratch *s)
 {
     if (pb->rk4) {
         rk4_step(pb, p, k, x, s);
+        return;
+    }
+    if (pb->implicit) {
+        implicit_step(pb, p, k, x, s);
         return;
     }
     int n = pb->n, m = pb->m;
@@ -538,7 +651,8 @@ int oracle_adjoint(const oracle_problem *pb, const double *params, const double 
                    double *dL_dp, double *dL_dx0)
 {
     /* the adjoint of the Euler-Maruyama recursion only */
-    if (oracle_check_problem(pb) != 0 || count < 0 || pb->steps > 0xffffffffLL || pb->rk4 || pb->milstein)
+    if (oracle_check_problem(pb) != 0 || count < 0 || pb->steps > 0xffffffffLL || pb->rk4 || pb->milstein ||
+        pb->implicit)
         return -1;
     int n = pb->n, m = pb->m, d = pb->d;
     int64_t K = pb->steps;

@@ -45,7 +45,12 @@ typedef struct {
     int32_t mean_field;      /* Kuramoto only: 1 = drift via (C, S) sums, 0 = pairwise definition */
     int32_t milstein;        /* 1: Milstein step instead of Euler-Maruyama (diagonal noise) */
     int32_t rk4;             /* 1: classical fourth-order Runge-Kutta on the drift alone (ODE path) */
+    int32_t implicit;        /* ODE path, drift alone: 1 implicit Euler, 2 implicit midpoint */
 } oracle_problem;
+
+/* Newton iterations per implicit step (a fixed count, started from the old
+ * state). */
+#define ORACLE_NEWTON_ITERS 4
 
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel
  * random numbers: as easy as 1, 2, 3").  ctr[4] counter, key[2] key. */
@@ -88,6 +93,10 @@ int oracle_diffusion(const oracle_problem *pb, double t, const double *x, const 
  *   1/2 g_jj dg_jj/dx_j (dW_j^2 - dt),   dW_j = sqrt(dt) N_j. */
 int oracle_diffusion_diag_derivative(const oracle_problem *pb, double t, const double *x, const double *p,
                                      double *dg);
+
+/* The drift's Jacobian J[i * n + j] = d f_i / d x_j, written out from each
+ * model's drift (the implicit ODE schemes' Newton iterations use it). */
+int oracle_drift_jacobian(const oracle_problem *pb, double t, const double *x, const double *p, double *J);
 
 /* Check n, m, d against the model; 0 = consistent. */
 int oracle_check_problem(const oracle_problem *pb);
