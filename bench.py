@@ -352,7 +352,7 @@ def run_ours(args):
     if not args.no_fhn:
         fhn = _time_fhn(stream, rank)
 
-    # ---- the ODE path: fourth-order Runge-Kutta on the Kuramoto drift -------
+    # ---- the ODE path: Runge-Kutta and the implicit schemes on the Kuramoto drift
     rk4 = None
     if not args.no_rk4:
         rk4 = _time_rk4(stream, rank)
@@ -648,9 +648,10 @@ def _paper_accuracy_protocol(stream, rank):
 
 
 def _time_rk4(stream, rank, reps=3, steps=1000):
-    """The ODE path: classical fourth-order Runge-Kutta on the drift of the
-    n = 32 benchmark problem (2^18 orbits, dt = 0.005, frame every 100 steps),
-    FP32, first 1000 steps, beside Euler-Maruyama on the same steps."""
+    """The ODE path: classical fourth-order Runge-Kutta, implicit Euler and
+    the implicit midpoint rule (4 Newton iterations a step) on the drift of
+    the n = 32 benchmark problem (2^18 orbits, dt = 0.005, frame every 100
+    steps), FP32, first 1000 steps, beside Euler-Maruyama on the same steps."""
     import torch
 
     import paper_1908_03869_gb300 as sdeb
@@ -664,9 +665,11 @@ def _time_rk4(stream, rank, reps=3, steps=1000):
     xt = torch.tensor(x0, dtype=torch.float32, device="cuda")
     out = {"workload": "Kuramoto n = 32, 2^18 orbits, dt = %g, first %d steps, frame every %d steps, fp32"
                        % (DT, steps, STRIDE)}
-    for name, rk in (("euler_maruyama", False), ("rk4", True)):
+    schemes = (("euler_maruyama", {}), ("rk4", {"rk4": True}), ("implicit_euler", {"implicit": "euler"}),
+               ("implicit_midpoint", {"implicit": "midpoint"}))
+    for name, kw in schemes:
         pb = sdeb.Problem.make("kuramoto", n, orbits, DT, steps, STRIDE, SEED, "fp32",
-                               orbit_offset=weak_scaling_offset(orbits, rank), rk4=rk)
+                               orbit_offset=weak_scaling_offset(orbits, rank), **kw)
         times = []
         with Integrator(pb) as it:
             for _ in range(reps + 1):
@@ -683,6 +686,10 @@ def _time_rk4(stream, rank, reps=3, steps=1000):
     # four drift evaluations per step, each a sin and a cos per oscillator
     out["sfu_roofline_frac_rk4"] = 8.0 * n * out["rk4"]["orbit_steps_per_sec"] / peak
     out["rk4_time_over_em"] = out["rk4"]["ms"] / out["euler_maruyama"]["ms"]
+    # four Newton iterations per step, each a sin, a cos and a reciprocal per oscillator
+    for name in ("implicit_euler", "implicit_midpoint"):
+        out["sfu_roofline_frac_" + name] = 12.0 * n * out[name]["orbit_steps_per_sec"] / peak
+        out[name + "_time_over_em"] = out[name]["ms"] / out["euler_maruyama"]["ms"]
     return out
 
 

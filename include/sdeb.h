@@ -121,7 +121,23 @@ enum {
      * layouts sdeb_create picks (sdeb_set_layout to another layout returns
      * EUNSUPPORTED at integration).  Exclusive with SDEB_FLAG_MILSTEIN
      * (EINVAL); sdeb_grad and batches return EUNSUPPORTED. */
-    SDEB_FLAG_RK4 = 8u
+    SDEB_FLAG_RK4 = 8u,
+    /* The ODE path, implicit Euler on the drift alone (the paper lists the
+     * implicit Euler method among its ODE integrators, Sec. 1.2):
+     * y = x + h f(t + h, y), solved by 4 Newton iterations from y = x, each
+     * with the exact Jacobian of the built-in model's drift (a closed-form
+     * solve: diagonal plus rank 2 for the Kuramoto models, which needs
+     * K dt < 1; 2 x 2 blocks plus rank 1 for SDEB_FHN_NET; scalar for the
+     * others).  The diffusion is not applied and no noise is drawn.  Built-in
+     * models only (EUNSUPPORTED for SDEB_USER), the layouts sdeb_create picks;
+     * exclusive with SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4 and
+     * SDEB_FLAG_IMPLICIT_MIDPOINT (EINVAL); sdeb_grad and batches return
+     * EUNSUPPORTED. */
+    SDEB_FLAG_IMPLICIT_EULER = 16u,
+    /* As SDEB_FLAG_IMPLICIT_EULER with the implicit midpoint rule,
+     * y = x + h f(t + h/2, (x + y) / 2) (Sec. 1.2's implicit midpoint
+     * method); the Kuramoto solve needs K dt < 2. */
+    SDEB_FLAG_IMPLICIT_MIDPOINT = 32u
 };
 
 typedef struct {

@@ -401,9 +401,6 @@ static void rk4_step(const oracle_problem *pb, const double *p, int64_t k, doubl
         x[i] += h * (s->k[0][i] + 2.0 * s->k[1][i] + 2.0 * s->k[2][i] + s->k[3][i]) / 6.0;
 }
 
-/* One step of Eq. 2 at step index k (reading of Eq. 2's t: the drift and
- * diffusion of step k are evaluated at t_k = t0 + k dt and at the old state,
- * the update of all components is simultaneous). */
 /* One step of an implicit ODE scheme on the drift alone (the paper lists
  * implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.2):
  *   implicit Euler:    y = x + h f(t + h, y),
@@ -432,6 +429,9 @@ static void implicit_step(const oracle_problem *pb, const double *p, int64_t k, 
     memcpy(x, y, sizeof(double) * (size_t)n);
 }
 
+/* One step of Eq. 2 at step index k (reading of Eq. 2's t: the drift and
+ * diffusion of step k are evaluated at t_k = t0 + k dt and at the old state,
+ * the update of all components is simultaneous). */
 static void em_step(const oracle_problem *pb, const double *p, int64_t k, uint32_t orbit,
                     double *x, em_scratch *s)
 {

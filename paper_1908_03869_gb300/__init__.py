@@ -21,7 +21,7 @@ __all__ = [
     "SDEB_KURAMOTO", "SDEB_KURAMOTO_PAPER", "SDEB_FHN_NET", "SDEB_OU", "SDEB_GBM", "SDEB_LINEAR_ODE",
     "SDEB_USER", "SDEB_USER_MAX_N", "SDEB_USER_MAX_M", "sdeb_create_user",
     "SDEB_FP32_KAHAN", "SDEB_FP64", "SDEB_FLAG_SHARED_PARAMS", "SDEB_FLAG_NO_FRAMES", "SDEB_FLAG_MILSTEIN",
-    "SDEB_FLAG_RK4",
+    "SDEB_FLAG_RK4", "SDEB_FLAG_IMPLICIT_EULER", "SDEB_FLAG_IMPLICIT_MIDPOINT",
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
@@ -35,6 +35,8 @@ SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER, SDEB_FHN_NET, SDEB_OU, SDEB_GBM, SDEB_LINEAR
 SDEB_USER_MAX_N = SDEB_USER_MAX_M = 64
 SDEB_FP32_KAHAN, SDEB_FP64 = 0, 1
 SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES, SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4 = 1, 2, 4, 8
+SDEB_FLAG_IMPLICIT_EULER, SDEB_FLAG_IMPLICIT_MIDPOINT = 16, 32
+IMPLICIT_FLAGS = {None: 0, "euler": SDEB_FLAG_IMPLICIT_EULER, "midpoint": SDEB_FLAG_IMPLICIT_MIDPOINT}
 
 MODEL_IDS = {
     "kuramoto": SDEB_KURAMOTO, "kuramoto_paper": SDEB_KURAMOTO_PAPER, "fhn_net": SDEB_FHN_NET,
@@ -64,7 +66,9 @@ class Problem(ctypes.Structure):
 
     @classmethod
     def make(cls, model, n, orbits, dt, steps, stride=1, seed=0, precision="fp32", t0=0.0, ckpt_every=0,
-             shared_params=False, no_frames=False, orbit_offset=0, m=None, d=None, milstein=False, rk4=False):
+             shared_params=False, no_frames=False, orbit_offset=0, m=None, d=None, milstein=False, rk4=False,
+             implicit=None):
+        """implicit: None, "euler" or "midpoint" (the implicit ODE schemes)."""
         mid = MODEL_IDS.get(model, model)
         if mid == SDEB_USER:
             if m is None or d is None:
@@ -73,7 +77,7 @@ class Problem(ctypes.Structure):
         else:
             m0, d0 = model_shape(mid, n) if mid in MODEL_IDS.values() else (0, 0)
         flags = (SDEB_FLAG_SHARED_PARAMS if shared_params else 0) | (SDEB_FLAG_NO_FRAMES if no_frames else 0) | \
-            (SDEB_FLAG_MILSTEIN if milstein else 0) | (SDEB_FLAG_RK4 if rk4 else 0)
+            (SDEB_FLAG_MILSTEIN if milstein else 0) | (SDEB_FLAG_RK4 if rk4 else 0) | IMPLICIT_FLAGS[implicit]
         return cls(mid, n, m0 if m is None else m, d0 if d is None else d, orbits, t0, dt, steps, stride,
                    seed & 0xFFFFFFFFFFFFFFFF, PRECISIONS.get(precision, precision), ckpt_every, flags, 0,
                    orbit_offset)

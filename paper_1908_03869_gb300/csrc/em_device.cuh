@@ -119,6 +119,16 @@ __device__ __forceinline__ float lg2_approx_f32(float y) {
     return r;
 }
 
+// Reciprocal for the Newton solves of the implicit schemes: in FP32 the SFU's
+// rcp.approx.ftz (an inexact Jacobian solve only perturbs a Newton
+// correction at the level of its own rounding), in FP64 the quotient.
+__device__ __forceinline__ float recip_fast(float y) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+    return r;
+}
+__device__ __forceinline__ double recip_fast(double y) { return 1.0 / y; }
+
 __device__ __forceinline__ void sincos_approx_f32(float x, float &s, float &c) {
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));

@@ -161,17 +161,17 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
 }
 
 // One stage of the classical fourth-order Runge-Kutta step (below): the
-// coupling sums at `at` (with compensation words ca), then per unit the
+// coupling sums at the stage state `at`, then per unit the
 // model's increment with a zero normal, h f(at); acc += weight h f(at), and
 // y = base + frac_next h f(at) is the next stage's state (y may be `at`:
 // each unit is read before it is overwritten, the sums were taken first).
 template <class M, typename Real, int P, class RED>
-__device__ __forceinline__ void rk4_stage(M &model, const Real (&at)[M::U][P], const Real (&ca)[M::U][P],
-                                          const Real (&base)[M::U][P], int u0, int units, RED &reduce,
-                                          Real (&acc)[M::U][P], Real (&y)[M::U][P], Real weight, Real frac_next) {
+__device__ __forceinline__ void rk4_stage(M &model, const Real (&at)[M::U][P], const Real (&base)[M::U][P],
+                                          int u0, int units, RED &reduce, Real (&acc)[M::U][P], Real (&y)[M::U][P],
+                                          Real weight, Real frac_next) {
     constexpr int NRA = M::NR > 0 ? M::NR : 1;
     Real red[NRA];
-    model.prepare(at, ca, u0, units, red);
+    model.prepare_stage(at, u0, units, red);
     if constexpr (M::NR > 0) reduce(red);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -196,26 +196,77 @@ __device__ __forceinline__ void rk4_stage(M &model, const Real (&at)[M::U][P], c
 template <class M, typename Real, int P, class RED>
 __device__ __forceinline__ void rk4_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], int u0, int units,
                                          RED &reduce) {
-    Real acc[M::U][P], y[M::U][P], base[M::U][P], none[M::U][P];
+    Real acc[M::U][P], y[M::U][P], base[M::U][P];
 #pragma unroll
     for (int c = 0; c < M::U; ++c)
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            acc[c][i] = Real(0);
-            none[c][i] = Real(0);
-        }
+        for (int i = 0; i < P; ++i) acc[c][i] = Real(0);
     model.stage_base(x, cp, base);
-    rk4_stage<M, Real, P>(model, x, cp, base, u0, units, reduce, acc, y, Real(1), Real(0.5));
-    rk4_stage<M, Real, P>(model, y, none, base, u0, units, reduce, acc, y, Real(2), Real(0.5));
-    rk4_stage<M, Real, P>(model, y, none, base, u0, units, reduce, acc, y, Real(2), Real(1));
-    rk4_stage<M, Real, P>(model, y, none, base, u0, units, reduce, acc, y, Real(1), Real(0));
+    rk4_stage<M, Real, P>(model, base, base, u0, units, reduce, acc, y, Real(1), Real(0.5));
+    rk4_stage<M, Real, P>(model, y, base, u0, units, reduce, acc, y, Real(2), Real(0.5));
+    rk4_stage<M, Real, P>(model, y, base, u0, units, reduce, acc, y, Real(2), Real(1));
+    rk4_stage<M, Real, P>(model, y, base, u0, units, reduce, acc, y, Real(1), Real(0));
 #pragma unroll
     for (int i = 0; i < P; ++i)
 #pragma unroll
         for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], mul_r(acc[c][i], Real(1) / Real(6)));
 }
 
-template <class M, typename Real, int G, int P, bool RK4>
+// Newton iterations per implicit step (a fixed count, from the old state).
+constexpr int kNewtonIters = 4;
+
+// One step of an implicit ODE scheme on the drift alone (the paper lists
+// implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.2):
+// the increment d solves d = h f(x + theta d) -- theta = 1 implicit Euler,
+// 1/2 implicit midpoint -- by kNewtonIters Newton iterations from d = 0:
+// at z = x + theta d the residual r = h f(z) - d (the model's increment with
+// a zero normal), then d += (I - theta h J(z))^-1 r, the solve done by the
+// model in closed form for its Jacobian's structure.  d then goes through
+// the compensated accumulation.  No noise is drawn.  z is built on the
+// model's stage base, as the Runge-Kutta stages are.
+template <class M, typename Real, int P, class RED>
+__device__ __forceinline__ void implicit_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], int u0, int units,
+                                              RED &reduce, Real theta) {
+    constexpr int NRA = M::NR > 0 ? M::NR : 1;
+    Real base[M::U][P], d[M::U][P], z[M::U][P];
+    model.stage_base(x, cp, base);
+#pragma unroll
+    for (int c = 0; c < M::U; ++c)
+#pragma unroll
+        for (int i = 0; i < P; ++i) d[c][i] = Real(0);
+#pragma unroll 1
+    for (int it = 0; it < kNewtonIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < M::U; ++c)
+#pragma unroll
+            for (int i = 0; i < P; ++i) z[c][i] = fma_r(theta, d[c][i], base[c][i]);
+        Real red[NRA];
+        model.prepare_stage(z, u0, units, red);
+        if constexpr (M::NR > 0) reduce(red);
+        Real r[M::U][P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            Real inc[M::U];
+            model.incr(i, z, red, Real(0), inc);
+#pragma unroll
+            for (int c = 0; c < M::U; ++c) r[c][i] = inc[c] - d[c][i];
+        }
+        model.newton_solve(z, red, r, theta, u0, units, reduce);
+#pragma unroll
+        for (int c = 0; c < M::U; ++c)
+#pragma unroll
+            for (int i = 0; i < P; ++i) d[c][i] += r[c][i];
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+#pragma unroll
+        for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], d[c][i]);
+}
+
+// Step schemes of the forward kernel.
+enum : int { kSchemeEm = 0, kSchemeRk4 = 1, kSchemeImplicit = 2 };
+
+template <class M, typename Real, int G, int P, int SCHEME>
 __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     constexpr int U = M::U;
     constexpr bool kKahan = std::is_same<Real, float>::value;
@@ -265,8 +316,10 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
         const uint32_t run = (uint32_t)(k_stop - k);
 #pragma unroll kRunUnroll
         for (uint32_t s = 0; s < run; ++s) {
-            if constexpr (RK4)
+            if constexpr (SCHEME == kSchemeRk4)
                 rk4_step<M, Real, P>(model, x, cp, u0, units, reduce);
+            else if constexpr (SCHEME == kSchemeImplicit)
+                implicit_step<M, Real, P>(model, x, cp, u0, units, reduce, a.implicit == 1 ? Real(1) : Real(0.5));
             else
                 em_step<M, Real, P>(model, x, cp, k + s, gorb, u0, units, a.keys, reduce);
         }
@@ -309,9 +362,9 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     }
 }
 
-template <class M, typename Real, int G, int P, bool RK4>
+template <class M, typename Real, int G, int P, int SCHEME>
 __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const ForwardArgs a) {
-    em_forward_body<M, Real, G, P, RK4>(a);
+    em_forward_body<M, Real, G, P, SCHEME>(a);
 }
 
 // The same kernel with registers capped so that five blocks fit per SM: used
@@ -321,31 +374,31 @@ __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const Forward
 // layouts keep the compiler's choice (96 registers already).
 template <class M, typename Real, int G, int P>
 __global__ void __launch_bounds__(kForwardBlock, 5) em_forward_kernel_5blocks(const ForwardArgs a) {
-    em_forward_body<M, Real, G, P, false>(a);
+    em_forward_body<M, Real, G, P, kSchemeEm>(a);
 }
 
 template <class M, typename Real, int G, int P>
 constexpr bool kForwardFiveBlocks = std::is_same<Real, float>::value && G > 1 && M::U == 1 && P <= 8;
 
-// RK4: the Runge-Kutta instantiation (the ODE path), else Euler-Maruyama or
-// Milstein (chosen by the model functor).
-template <template <typename, int> class MF, typename Real, int G, int P, bool RK4 = false>
+// SCHEME: kSchemeEm (Euler-Maruyama, or Milstein chosen by the model
+// functor), or an ODE-path scheme (kSchemeRk4, kSchemeImplicit).
+template <template <typename, int> class MF, typename Real, int G, int P, int SCHEME = kSchemeEm>
 cudaError_t launch_forward_layout(const ForwardArgs &a, cudaStream_t s) {
     using M = MF<Real, P>;
     const int64_t threads = a.orbits * G;
     const int64_t grid = (threads + kForwardBlock - 1) / kForwardBlock;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if constexpr (!RK4 && kForwardFiveBlocks<M, Real, G, P>)
+    if constexpr (SCHEME == kSchemeEm && kForwardFiveBlocks<M, Real, G, P>)
         em_forward_kernel_5blocks<M, Real, G, P><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     else
-        em_forward_kernel<M, Real, G, P, RK4><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
+        em_forward_kernel<M, Real, G, P, SCHEME><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 #define SDEB_FORWARD_LAYOUT(G_, P_) \
     if (l.G == (G_) && l.P == (P_)) return launch_forward_layout<MF, Real, G_, P_>(a, s);
-#define SDEB_FORWARD_LAYOUT_RK4(G_, P_) \
-    if (l.G == (G_) && l.P == (P_)) return launch_forward_layout<MF, Real, G_, P_, true>(a, s);
+#define SDEB_FORWARD_LAYOUT_ODE(G_, P_) \
+    if (l.G == (G_) && l.P == (P_)) return launch_forward_layout<MF, Real, G_, P_, SCHEME>(a, s);
 
 // The layouts default_layout() can return.
 template <template <typename, int> class MF, typename Real>
@@ -362,18 +415,18 @@ cudaError_t dispatch_default_layouts(const ForwardArgs &a, Layout l, cudaStream_
     return cudaErrorNotSupported;
 }
 
-// The Runge-Kutta instantiations, for the layouts default_layout() can return.
-template <template <typename, int> class MF, typename Real>
-cudaError_t dispatch_rk4_layouts(const ForwardArgs &a, Layout l, cudaStream_t s) {
-    SDEB_FORWARD_LAYOUT_RK4(1, 1)
-    SDEB_FORWARD_LAYOUT_RK4(1, 2)
-    SDEB_FORWARD_LAYOUT_RK4(1, 4)
-    SDEB_FORWARD_LAYOUT_RK4(1, 8)
-    SDEB_FORWARD_LAYOUT_RK4(2, 8)
-    SDEB_FORWARD_LAYOUT_RK4(4, 8)
-    SDEB_FORWARD_LAYOUT_RK4(8, 8)
-    SDEB_FORWARD_LAYOUT_RK4(16, 8)
-    SDEB_FORWARD_LAYOUT_RK4(32, 8)
+// The ODE-path instantiations (SCHEME), for the layouts default_layout() can return.
+template <template <typename, int> class MF, typename Real, int SCHEME>
+cudaError_t dispatch_ode_layouts(const ForwardArgs &a, Layout l, cudaStream_t s) {
+    SDEB_FORWARD_LAYOUT_ODE(1, 1)
+    SDEB_FORWARD_LAYOUT_ODE(1, 2)
+    SDEB_FORWARD_LAYOUT_ODE(1, 4)
+    SDEB_FORWARD_LAYOUT_ODE(1, 8)
+    SDEB_FORWARD_LAYOUT_ODE(2, 8)
+    SDEB_FORWARD_LAYOUT_ODE(4, 8)
+    SDEB_FORWARD_LAYOUT_ODE(8, 8)
+    SDEB_FORWARD_LAYOUT_ODE(16, 8)
+    SDEB_FORWARD_LAYOUT_ODE(32, 8)
     return cudaErrorNotSupported;
 }
 

@@ -6,8 +6,21 @@
 #include <cuda_runtime.h>
 
 #include "em_device.cuh"
+#include "sdeb.h"
 
 namespace sdeb {
+
+// The step-scheme flags of sdeb_problem.flags; at most one may be set.
+constexpr uint32_t kImplicitFlags = SDEB_FLAG_IMPLICIT_EULER | SDEB_FLAG_IMPLICIT_MIDPOINT;
+constexpr uint32_t kSchemeFlags = SDEB_FLAG_MILSTEIN | SDEB_FLAG_RK4 | kImplicitFlags;
+inline bool scheme_flags_valid(uint32_t flags) {
+    const uint32_t f = flags & kSchemeFlags;
+    return (f & (f - 1u)) == 0u;
+}
+// ForwardArgs::implicit of the flags: 1 implicit Euler, 2 implicit midpoint, 0 neither.
+inline int32_t implicit_kind(uint32_t flags) {
+    return (flags & SDEB_FLAG_IMPLICIT_EULER) ? 1 : (flags & SDEB_FLAG_IMPLICIT_MIDPOINT) ? 2 : 0;
+}
 
 enum ModelId : int32_t {
     kKuramoto = 1,
@@ -46,6 +59,7 @@ struct ForwardArgs {
     PhiloxKeys keys;
     int32_t milstein;  // 1: Milstein step (models with multiplicative noise), 0: Euler-Maruyama
     int32_t rk4;       // 1: fourth-order Runge-Kutta on the drift alone (launch_forward_rk4_*)
+    int32_t implicit;  // 1: implicit Euler, 2: implicit midpoint on the drift alone (launch_forward_implicit_*)
 };
 
 // Returns cudaSuccess or the launch error; cudaErrorNotSupported when the
@@ -56,10 +70,13 @@ cudaError_t launch_forward_other_f32(const ForwardArgs &a, Layout l, cudaStream_
 cudaError_t launch_forward_other_f64(const ForwardArgs &a, Layout l, cudaStream_t s);
 cudaError_t launch_forward_rk4_f32(const ForwardArgs &a, Layout l, cudaStream_t s);
 cudaError_t launch_forward_rk4_f64(const ForwardArgs &a, Layout l, cudaStream_t s);
+cudaError_t launch_forward_implicit_f32(const ForwardArgs &a, Layout l, cudaStream_t s);
+cudaError_t launch_forward_implicit_f64(const ForwardArgs &a, Layout l, cudaStream_t s);
 
-// The forward launch of a problem: Runge-Kutta, phase models or the others.
+// The forward launch of a problem: Runge-Kutta, implicit, phase models or the others.
 inline cudaError_t launch_forward_any(const ForwardArgs &a, Layout l, bool fp64, cudaStream_t s) {
     if (a.rk4) return fp64 ? launch_forward_rk4_f64(a, l, s) : launch_forward_rk4_f32(a, l, s);
+    if (a.implicit) return fp64 ? launch_forward_implicit_f64(a, l, s) : launch_forward_implicit_f32(a, l, s);
     const bool phase = a.model == kKuramoto || a.model == kKuramotoPaper;
     if (phase) return fp64 ? launch_forward_kuramoto_f64(a, l, s) : launch_forward_kuramoto_f32(a, l, s);
     return fp64 ? launch_forward_other_f64(a, l, s) : launch_forward_other_f32(a, l, s);

@@ -11,9 +11,18 @@
 //   prepare(x, cp, u0, units, red)    per-lane partial coupling sums (and any
 //                                     per-unit value reused by incr); cp is
 //                                     the Kahan compensation (zero in FP64)
+//   prepare_stage(z, u0, units, red)  prepare for a stage state of the ODE
+//                                     schemes, built on stage_base (no
+//                                     compensation word; a phase within a
+//                                     step of [-pi, pi] is not reduced again)
 //   incr(i, x, red, N, inc)           the Eq. 2 increment f dt + g sqrt(dt) N
 //                                     of unit i's components, after red has
 //                                     been summed over the G lanes.
+//   newton_solve(z, red, r, theta,    r <- (I - theta dt J(z))^-1 r for the
+//                u0, units, reduce)   implicit ODE schemes, J the drift's
+//                                     Jacobian, after prepare(z) and the sums
+//                                     red; padding units do not enter its
+//                                     sums.
 // State component c of unit j lives at x[c * units + j] in the orbit's row.
 #pragma once
 
@@ -50,8 +59,8 @@ struct KuramotoLane {
         }
     }
 
-    // Base of the Runge-Kutta stage states: the compensated phase reduced to
-    // [-pi, pi] (sin and cos are 2 pi periodic; the stages see the phase
+    // Base of the ODE schemes' stage states: the compensated phase reduced
+    // to [-pi, pi] (sin and cos are 2 pi periodic; the stages see the phase
     // with the rounding of a number below pi).
     __device__ __forceinline__ void stage_base(const Real (&x)[U][P], const Real (&cp)[U][P],
                                                Real (&base)[U][P]) const {
@@ -73,12 +82,58 @@ struct KuramotoLane {
         red[1] = S;
     }
 
+    __device__ __forceinline__ void prepare_stage(const Real (&z)[U][P], int, int, Real (&red)[NR]) {
+        Real C = 0, S = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            sincos_reduced(z[0][i], sn[i], cs[i]);
+            C = fma_r(live[i], cs[i], C);
+            S = fma_r(live[i], sn[i], S);
+        }
+        red[0] = C;
+        red[1] = S;
+    }
+
     // f dt + g sqrt(dt) N = (K/n) dt (S cos - C sin) + (omega dt + g sqrt(dt) N)
     __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&red)[NR], Real N,
                                          Real (&inc)[U]) const {
         (void)x;
         const Real coupling = fma_r(red[1], cs[i], -mul_r(red[0], sn[i]));  // S cos - C sin
         inc[0] = fma_r(kn_dt, coupling, fma_r(gsq[PAPER ? i : 0], N, omega_dt[i]));
+    }
+
+    // With c_i = cos z_i, s_i = sin z_i the drift's Jacobian is
+    // (K/n) (c c^T + s s^T) - diag((K/n) (C c_i + S s_i)), so
+    // I - theta dt J = D - beta U U^T with U = [c s], beta = theta (K/n) dt,
+    // D = diag(1 + beta (C c_i + S s_i)): solved by the Woodbury identity,
+    // w = D^-1 r, m = U^T D^-1 U and q = U^T w summed over the orbit's units,
+    // r <- w + beta D^-1 U (I - beta m)^-1 q.  D is nonsingular while
+    // theta K dt < 1.  Padding units get a zero correction.
+    template <class RED>
+    __device__ __forceinline__ void newton_solve(const Real (&)[U][P], const Real (&red)[NR], Real (&r)[U][P],
+                                                 Real theta, int, int, RED &reduce) const {
+        const Real C = red[0], S = red[1], beta = theta * kn_dt;
+        Real inv_a[P], m[2] = {Real(0), Real(0)}, q[2] = {Real(0), Real(0)}, m22[1] = {Real(0)};
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            inv_a[i] = live[i] * recip_fast(fma_r(beta, fma_r(C, cs[i], mul_r(S, sn[i])), Real(1)));
+            const Real w = r[0][i] * inv_a[i];
+            const Real tc = cs[i] * inv_a[i], ts = sn[i] * inv_a[i];
+            r[0][i] = w;
+            m[0] = fma_r(cs[i], tc, m[0]);
+            m[1] = fma_r(sn[i], tc, m[1]);
+            m22[0] = fma_r(sn[i], ts, m22[0]);
+            q[0] = fma_r(cs[i], w, q[0]);
+            q[1] = fma_r(sn[i], w, q[1]);
+        }
+        reduce(m);
+        reduce(q);
+        reduce(m22);
+        const Real e11 = Real(1) - beta * m[0], e22 = Real(1) - beta * m22[0], e12 = -beta * m[1];
+        const Real inv_det = recip_fast(e11 * e22 - e12 * e12);
+        const Real z1 = (e22 * q[0] - e12 * q[1]) * inv_det, z2 = (e11 * q[1] - e12 * q[0]) * inv_det;
+#pragma unroll
+        for (int i = 0; i < P; ++i) r[0][i] = fma_r(beta * inv_a[i], fma_r(cs[i], z1, sn[i] * z2), r[0][i]);
     }
 };
 
@@ -102,7 +157,7 @@ struct FhnLane {
     Real a, b, eps, I, c, gsq, dt, inv_units;
     Real half_gsq2;  // (sigma sqrt(dt))^2 / 2, the Milstein coefficient
 
-    // Base of the Runge-Kutta stage states: the state itself.
+    // Base of the ODE schemes' stage states: the state itself.
     __device__ __forceinline__ void stage_base(const Real (&x)[U][P], const Real (&)[U][P],
                                                Real (&base)[U][P]) const {
 #pragma unroll
@@ -132,6 +187,10 @@ struct FhnLane {
         red[0] = sv;
     }
 
+    __device__ __forceinline__ void prepare_stage(const Real (&z)[U][P], int u0, int units, Real (&red)[NR]) {
+        prepare(z, z, u0, units, red);
+    }
+
     __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&red)[NR], Real N,
                                          Real (&inc)[U]) const {
         Real v = x[0][i], w = x[1][i];
@@ -141,6 +200,43 @@ struct FhnLane {
         inc[0] = fv * dt + gsq * v * N;
         if constexpr (MIL) inc[0] += milstein_multiplicative(half_gsq2, v, N);
         inc[1] = fw * dt;
+    }
+
+    // I - theta dt J is block diagonal, E_i = [[1 - th (1 - v_i^2 - c), th],
+    // [-th eps, 1 + th eps b]] with th = theta dt, minus the mean-field
+    // coupling's rank-1 term gamma e e^T (e: 1 on every v, gamma = th c / u):
+    // by Sherman-Morrison, p = E^-1 r and q = E^-1 e unit by unit, P and Q
+    // the sums of their v parts over the orbit's units,
+    // r <- p + gamma P / (1 - gamma Q) q.
+    template <class RED>
+    __device__ __forceinline__ void newton_solve(const Real (&z)[U][P], const Real (&)[NR], Real (&r)[U][P],
+                                                 Real theta, int u0, int units, RED &reduce) const {
+        const Real th = theta * dt, gamma = th * c * inv_units;
+        const Real e12 = th, e21 = -th * eps, e22 = Real(1) + th * eps * b;
+        Real qv[P], qw[P], sums[2] = {Real(0), Real(0)};
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const Real v = z[0][i];
+            const Real e11 = Real(1) - th * (Real(1) - v * v - c);
+            const Real inv_det = Real(1) / (e11 * e22 - e12 * e21);
+            const Real pv = (e22 * r[0][i] - e12 * r[1][i]) * inv_det;
+            const Real pw = (e11 * r[1][i] - e21 * r[0][i]) * inv_det;
+            r[0][i] = pv;
+            r[1][i] = pw;
+            qv[i] = e22 * inv_det;
+            qw[i] = -e21 * inv_det;
+            if (u0 + i < units) {
+                sums[0] += pv;
+                sums[1] += qv[i];
+            }
+        }
+        reduce(sums);
+        const Real coef = gamma * sums[0] / (Real(1) - gamma * sums[1]);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            r[0][i] = fma_r(coef, qv[i], r[0][i]);
+            r[1][i] = fma_r(coef, qw[i], r[1][i]);
+        }
     }
 };
 
@@ -155,7 +251,7 @@ struct ScalarLane {
     static constexpr bool kNoise = KIND != 2;
     Real rate, gsq, dt, half_gsq2;
 
-    // Base of the Runge-Kutta stage states: the state itself.
+    // Base of the ODE schemes' stage states: the state itself.
     __device__ __forceinline__ void stage_base(const Real (&x)[U][P], const Real (&)[U][P],
                                                Real (&base)[U][P]) const {
 #pragma unroll
@@ -171,6 +267,7 @@ struct ScalarLane {
 
     __device__ __forceinline__ void prepare(const Real (&)[U][P], const Real (&)[U][P], int, int,
                                             Real (&)[NR > 0 ? NR : 1]) {}
+    __device__ __forceinline__ void prepare_stage(const Real (&)[U][P], int, int, Real (&)[NR > 0 ? NR : 1]) {}
 
     __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&)[NR > 0 ? NR : 1],
                                          Real N, Real (&inc)[U]) const {
@@ -181,6 +278,17 @@ struct ScalarLane {
             if constexpr (MIL) inc[0] += milstein_multiplicative(half_gsq2, xi, N);
         }
         if (KIND == 2) inc[0] = -rate * xi * dt;
+    }
+
+    // The drift is lambda x (lambda = rate for GBM, -rate otherwise):
+    // I - theta dt J = 1 - theta dt lambda.
+    template <class RED>
+    __device__ __forceinline__ void newton_solve(const Real (&)[U][P], const Real (&)[NR > 0 ? NR : 1],
+                                                 Real (&r)[U][P], Real theta, int, int, RED &) const {
+        const Real lambda = KIND == 1 ? rate : -rate;
+        const Real inv = Real(1) / (Real(1) - theta * dt * lambda);
+#pragma unroll
+        for (int i = 0; i < P; ++i) r[0][i] *= inv;
     }
 };
 

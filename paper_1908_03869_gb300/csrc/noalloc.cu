@@ -101,8 +101,8 @@ extern "C" sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void
     if (pb->orbits <= 0 || !(pb->dt > 0.0) || !std::isfinite(pb->dt) || !std::isfinite(pb->t0) ||
         pb->steps < 0 || pb->steps > 0xffffffffLL || pb->stride < 1 || pb->stride > 0xffffffffLL ||
         (pb->precision != SDEB_FP32_KAHAN && pb->precision != SDEB_FP64) || pb->reserved != 0 ||
-        (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES | SDEB_FLAG_MILSTEIN | SDEB_FLAG_RK4)) ||
-        ((pb->flags & SDEB_FLAG_MILSTEIN) && (pb->flags & SDEB_FLAG_RK4)) || pb->orbit_offset < 0 ||
+        (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES | kSchemeFlags)) ||
+        !scheme_flags_valid(pb->flags) || pb->orbit_offset < 0 ||
         pb->orbit_offset + pb->orbits > 0x100000000LL)
         return fail(SDEB_EINVAL, "problem fields out of range");
     if (pb->ckpt_every != 0) return fail(SDEB_EUNSUPPORTED, "checkpoints need the context API");
@@ -156,6 +156,7 @@ extern "C" sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void
     a.keys = philox_key_schedule(pb->seed);
     a.milstein = (pb->flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     a.rk4 = (pb->flags & SDEB_FLAG_RK4) ? 1 : 0;
+    a.implicit = implicit_kind(pb->flags);
     e = launch_forward_any(a, layout, fp64, s);
     if (e == cudaErrorNotSupported) return fail(SDEB_EUNSUPPORTED, "no kernel for this model and layout");
     if (e != cudaSuccess) return fail(SDEB_ECUDA, "forward kernel launch failed");

@@ -140,7 +140,7 @@ sdeb_status validate(const sdeb_problem *pb, int32_t &units) {
         if (pb->n > SDEB_USER_MAX_N || pb->m < 0 || pb->m > SDEB_USER_MAX_M || pb->d < 0)
             return fail(nullptr, SDEB_EINVAL, "a user model needs 1 <= n <= %d, 0 <= m <= %d, d >= 0",
                         SDEB_USER_MAX_N, SDEB_USER_MAX_M);
-        if (pb->flags & SDEB_FLAG_MILSTEIN)
+        if (pb->flags & (SDEB_FLAG_MILSTEIN | kImplicitFlags))
             return fail(nullptr, SDEB_EUNSUPPORTED, "user models integrate by Euler-Maruyama or SDEB_FLAG_RK4");
         if (pb->ckpt_every != 0) return fail(nullptr, SDEB_EUNSUPPORTED, "user models keep no checkpoints");
         m = pb->m;
@@ -161,10 +161,12 @@ sdeb_status validate(const sdeb_problem *pb, int32_t &units) {
     if (pb->precision != SDEB_FP32_KAHAN && pb->precision != SDEB_FP64)
         return fail(nullptr, SDEB_EINVAL, "unknown precision %d", pb->precision);
     if (pb->ckpt_every < 0) return fail(nullptr, SDEB_EINVAL, "ckpt_every must be >= 0");
-    if (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES | SDEB_FLAG_MILSTEIN | SDEB_FLAG_RK4))
+    if (pb->flags & ~(uint32_t)(SDEB_FLAG_SHARED_PARAMS | SDEB_FLAG_NO_FRAMES | kSchemeFlags))
         return fail(nullptr, SDEB_EINVAL, "unknown flag bits 0x%x", pb->flags);
-    if ((pb->flags & SDEB_FLAG_MILSTEIN) && (pb->flags & SDEB_FLAG_RK4))
-        return fail(nullptr, SDEB_EINVAL, "SDEB_FLAG_MILSTEIN and SDEB_FLAG_RK4 are exclusive");
+    if (!scheme_flags_valid(pb->flags))
+        return fail(nullptr, SDEB_EINVAL,
+                    "SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4, SDEB_FLAG_IMPLICIT_EULER and SDEB_FLAG_IMPLICIT_MIDPOINT "
+                    "are exclusive");
     if (pb->reserved != 0) return fail(nullptr, SDEB_EINVAL, "reserved field must be 0");
     if (pb->orbit_offset < 0 || pb->orbit_offset + pb->orbits > 0x100000000LL)
         return fail(nullptr, SDEB_EINVAL, "orbit_offset + orbits must not exceed 2^32");
@@ -527,7 +529,7 @@ sdeb_status build_batch_instances(const sdeb_problem *pbs, int32_t count, std::v
         if (pb.precision != pbs[0].precision || pb.seed != pbs[0].seed)
             return fail(nullptr, SDEB_EINVAL, "instance %d: precision and seed must match instance 0", i);
         if (pb.ckpt_every != 0) return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: no checkpoints in a batch", i);
-        if (pb.flags & SDEB_FLAG_RK4)
+        if (pb.flags & (SDEB_FLAG_RK4 | kImplicitFlags))
             return fail(nullptr, SDEB_EUNSUPPORTED, "instance %d: batches run Euler-Maruyama", i);
         if (pb.orbits > 0x7fffffffLL) return fail(nullptr, SDEB_EINVAL, "instance %d: too many orbits", i);
         const bool shared = pb.flags & SDEB_FLAG_SHARED_PARAMS;
@@ -796,6 +798,7 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
     a.keys = philox_key_schedule(ctx->pb.seed);
     a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     a.rk4 = (ctx->pb.flags & SDEB_FLAG_RK4) ? 1 : 0;
+    a.implicit = implicit_kind(ctx->pb.flags);
     cudaError_t e = launch_forward(a, ctx->layout, ctx->pb.precision == SDEB_FP64, as_stream(stream));
     if (e == cudaErrorNotSupported)
         return fail(ctx, SDEB_EUNSUPPORTED, "no kernel for model %d with layout G=%d P=%d", a.model,
@@ -899,7 +902,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
     // A context that keeps checkpoints for sdeb_grad is tuned for forward +
     // adjoint: both are timed over one segment (at most 1024 steps) from
     // checkpoint 0, which sdeb_set_params has written.
-    const bool tune_adjoint = ctx->d_seg != nullptr && !(ctx->pb.flags & (SDEB_FLAG_RK4 | SDEB_FLAG_MILSTEIN));
+    const bool tune_adjoint = ctx->d_seg != nullptr && !(ctx->pb.flags & (kSchemeFlags));
     if (trial_steps <= 0) trial_steps = 64;
     if (tune_adjoint) trial_steps = std::min<int64_t>((int64_t)ctx->pb.ckpt_every, 1024);
     if (trial_steps > ctx->pb.steps) trial_steps = ctx->pb.steps;
@@ -947,6 +950,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
         a.keys = philox_key_schedule(ctx->pb.seed);
         a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
         a.rk4 = (ctx->pb.flags & SDEB_FLAG_RK4) ? 1 : 0;
+        a.implicit = implicit_kind(ctx->pb.flags);
         float ms = 0.0f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
             e = cudaMemcpyAsync(tx, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
@@ -1035,7 +1039,7 @@ sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_d
     if (ctx->pb.model != SDEB_KURAMOTO && ctx->pb.model != SDEB_KURAMOTO_PAPER)
         return fail(ctx, SDEB_EUNSUPPORTED, "the adjoint is implemented for the Kuramoto models");
     if (ctx->pb.ckpt_every <= 0) return fail(ctx, SDEB_ESTATE, "context was created with ckpt_every = 0");
-    if (ctx->pb.flags & (SDEB_FLAG_RK4 | SDEB_FLAG_MILSTEIN))
+    if (ctx->pb.flags & kSchemeFlags)
         return fail(ctx, SDEB_EUNSUPPORTED, "sdeb_grad is the adjoint of the Euler-Maruyama step");
     if (!ctx->params_set || ctx->k_current != ctx->pb.steps)
         return fail(ctx, SDEB_ESTATE, "integrate to step %lld first (state is at %lld)", (long long)ctx->pb.steps,

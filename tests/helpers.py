@@ -25,7 +25,8 @@ def np_dtype(precision):
 
 
 def run_gpu(model, n, params, x0, dt, steps, stride, seed=0, precision="fp64", orbit_offset=0,
-            shared=False, no_frames=False, ranges=None, ckpt_every=0, milstein=False, layout=None, rk4=False):
+            shared=False, no_frames=False, ranges=None, ckpt_every=0, milstein=False, layout=None, rk4=False,
+            implicit=None):
     """Returns (frames or None, final) as numpy arrays in the context precision."""
     import torch
     from paper_1908_03869_gb300.integrator import Integrator
@@ -33,7 +34,7 @@ def run_gpu(model, n, params, x0, dt, steps, stride, seed=0, precision="fp64", o
     orbits = x0.shape[0]
     pb = sdeb.Problem.make(model, n, orbits, dt, steps, stride, seed, precision, orbit_offset=orbit_offset,
                            shared_params=shared, no_frames=no_frames, ckpt_every=ckpt_every, milstein=milstein,
-                           rk4=rk4)
+                           rk4=rk4, implicit=implicit)
     dt_t = torch.float64 if precision == "fp64" else torch.float32
     with Integrator(pb) as it:
         if layout is not None:
@@ -51,12 +52,12 @@ def run_gpu(model, n, params, x0, dt, steps, stride, seed=0, precision="fp64", o
 
 
 def run_oracle(model, n, params, x0, dt, steps, stride, seed=0, orbit_offset=0, shared=False,
-               mean_field=False, orbits=None, milstein=False, rk4=False):
+               mean_field=False, orbits=None, milstein=False, rk4=False, implicit=None):
     """Oracle on the same inputs (cast to float64).  orbits: optional index
     subset (global orbit index = orbit_offset + index)."""
     m, d = sdeb.model_shape(model, n)
     pb = oracle.make_problem(model, n, m, d, dt, steps, stride, seed, shared_params=shared,
-                             mean_field=mean_field, milstein=milstein, rk4=rk4)
+                             mean_field=mean_field, milstein=milstein, rk4=rk4, implicit=implicit)
     params = np.asarray(params, dtype=np.float64)
     x0 = np.asarray(x0, dtype=np.float64)
     if orbits is None:

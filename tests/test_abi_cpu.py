@@ -77,6 +77,14 @@ def test_validation_rejects_bad_problems(L):
     pb = sdeb.Problem.make(**good)
     pb.flags = 0x80
     assert _status(L, pb) == sdeb.SDEB_EINVAL
+    # at most one step scheme: Milstein, RK4, implicit Euler, implicit midpoint
+    for flags in (sdeb.SDEB_FLAG_MILSTEIN | sdeb.SDEB_FLAG_RK4,
+                  sdeb.SDEB_FLAG_RK4 | sdeb.SDEB_FLAG_IMPLICIT_EULER,
+                  sdeb.SDEB_FLAG_MILSTEIN | sdeb.SDEB_FLAG_IMPLICIT_MIDPOINT,
+                  sdeb.SDEB_FLAG_IMPLICIT_EULER | sdeb.SDEB_FLAG_IMPLICIT_MIDPOINT):
+        pb = sdeb.Problem.make(**good)
+        pb.flags = flags
+        assert _status(L, pb) == sdeb.SDEB_EINVAL, flags
     pb = sdeb.Problem.make(**good)
     pb.reserved = 1
     assert _status(L, pb) == sdeb.SDEB_EINVAL

@@ -47,6 +47,8 @@ def test_user_problem_validation():
     assert e.value.status == sdeb.SDEB_EINVAL
     for bad, status in ((_pb(n=65, m=1, d=1), sdeb.SDEB_EINVAL), (_pb(m=65), sdeb.SDEB_EINVAL),
                         (_pb(milstein=True), sdeb.SDEB_EUNSUPPORTED),
+                        (_pb(implicit="euler"), sdeb.SDEB_EUNSUPPORTED),
+                        (_pb(implicit="midpoint"), sdeb.SDEB_EUNSUPPORTED),
                         (_pb(ckpt_every=5), sdeb.SDEB_EUNSUPPORTED)):
         with pytest.raises(sdeb.SdebError) as e:
             sdeb.sdeb_create_user(bad, user_models.LINEAR_DENSE)
