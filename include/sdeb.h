@@ -249,11 +249,11 @@ SDEB_API sdeb_status sdeb_batch_plan(const sdeb_problem *pbs, int32_t count, dou
  * called but must still be defined).  One GPU thread per orbit.  The
  * context then works as one from sdeb_create (set_params, integrate,
  * integrate_range, read_orbits, read_final, orbit_flags); sdeb_set_layout,
- * sdeb_grad and SDEB_FLAG_MILSTEIN return EUNSUPPORTED, ckpt_every must be
- * 0, sdeb_autotune does nothing.  EINVAL with the compiler's log in
- * sdeb_last_error(NULL) when the source does not compile; EUNSUPPORTED when
- * the run-time compiler library (libnvrtc) cannot be loaded; ECUDA when the
- * compiled kernel cannot be loaded on the device. */
+ * sdeb_grad, SDEB_FLAG_MILSTEIN and the implicit-scheme flags return
+ * EUNSUPPORTED, ckpt_every must be 0, sdeb_autotune does nothing.  EINVAL
+ * with the compiler's log in sdeb_last_error(NULL) when the source does not
+ * compile; EUNSUPPORTED when the run-time compiler library (libnvrtc) cannot
+ * be loaded; ECUDA when the compiled kernel cannot be loaded on the device. */
 SDEB_API sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source, sdeb_ctx **out);
 
 /* Free the context and its device buffers (synchronises the device first).
