@@ -103,7 +103,7 @@ enum {
     SDEB_FLAG_SHARED_PARAMS = 1u, /* one parameter vector [d] for every orbit */
     SDEB_FLAG_NO_FRAMES = 2u,     /* keep only the final state (no frame buffer) */
     /* Milstein step instead of Euler-Maruyama (the scheme the paper names as
-     * the next one to add, Sec. 1.3 and Sec. 4; Kloeden and Platen's form
+     * the next one to add, Sec. 2.1 and Sec. 3; Kloeden and Platen's form
      * for diagonal noise): each Wiener channel j drives one state component
      * x_j with g_j(x_j), and the step adds 1/2 g_j g_j' (dW_j^2 - dt), dW_j =
      * sqrt(dt) N_j, to x_j.  This changes SDEB_GBM (g = sigma x) and the v
@@ -115,7 +115,7 @@ enum {
     SDEB_FLAG_MILSTEIN = 4u,
     /* The ODE path: classical fourth-order Runge-Kutta on the drift alone,
      * dx/dt = f(t, x, p) (the paper lists Runge-Kutta among its ODE
-     * integrators, Sec. 1.2): k1 = h f(x), k2 = h f(x + k1/2), k3 = h f(x +
+     * integrators, Sec. 1.5): k1 = h f(x), k2 = h f(x + k1/2), k3 = h f(x +
      * k2/2), k4 = h f(x + k3), x += (k1 + 2 k2 + 2 k3 + k4) / 6.  The
      * diffusion is not applied and no noise is drawn.  Every model, the
      * layouts sdeb_create picks (sdeb_set_layout to another layout returns
@@ -123,7 +123,7 @@ enum {
      * (EINVAL); sdeb_grad and batches return EUNSUPPORTED. */
     SDEB_FLAG_RK4 = 8u,
     /* The ODE path, implicit Euler on the drift alone (the paper lists the
-     * implicit Euler method among its ODE integrators, Sec. 1.2):
+     * implicit Euler method among its ODE integrators, Sec. 1.5):
      * y = x + h f(t + h, y), solved by 4 Newton iterations from y = x, each
      * with the exact Jacobian of the built-in model's drift (a closed-form
      * solve: diagonal plus rank 2 for the Kuramoto models, which needs
@@ -135,7 +135,7 @@ enum {
      * EUNSUPPORTED. */
     SDEB_FLAG_IMPLICIT_EULER = 16u,
     /* As SDEB_FLAG_IMPLICIT_EULER with the implicit midpoint rule,
-     * y = x + h f(t + h/2, (x + y) / 2) (Sec. 1.2's implicit midpoint
+     * y = x + h f(t + h/2, (x + y) / 2) (Sec. 1.5's implicit midpoint
      * method); the Kuramoto solve needs K dt < 2. */
     SDEB_FLAG_IMPLICIT_MIDPOINT = 32u
 };

@@ -383,7 +383,7 @@ static void scratch_free(em_scratch *s)
 
 /* One step of the classical fourth-order Runge-Kutta method on the drift
  * alone, dx/dt = f(t, x) (the ODE path; the paper lists Runge-Kutta among
- * the ODE integrators, Sec. 1.2):
+ * the ODE integrators, Sec. 1.5):
  *   k1 = f(t, x), k2 = f(t + h/2, x + h k1/2), k3 = f(t + h/2, x + h k2/2),
  *   k4 = f(t + h, x + h k3), x <- x + h (k1 + 2 k2 + 2 k3 + k4) / 6. */
 static void rk4_step(const oracle_problem *pb, const double *p, int64_t k, double *x, em_scratch *s)
@@ -402,7 +402,7 @@ static void rk4_step(const oracle_problem *pb, const double *p, int64_t k, doubl
 }
 
 /* One step of an implicit ODE scheme on the drift alone (the paper lists
- * implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.2):
+ * implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.5):
  *   implicit Euler:    y = x + h f(t + h, y),
  *   implicit midpoint: y = x + h f(t + h/2, (x + y) / 2),
  * solved by ORACLE_NEWTON_ITERS Newton iterations from y = x on

@@ -85,7 +85,7 @@ int oracle_drift(const oracle_problem *pb, double t, const double *x, const doub
 int oracle_diffusion(const oracle_problem *pb, double t, const double *x, const double *p, double *g);
 
 /* Milstein scheme support (the paper names the Milstein method as the next
- * integration scheme to add, Sec. 1.3 and Sec. 4; the scheme is Kloeden and
+ * integration scheme to add, Sec. 2.1 and Sec. 3; the scheme is Kloeden and
  * Platen's, "Numerical Solution of Stochastic Differential Equations",
  * Sec. 10.3).  Every model here has diagonal noise whose channel j drives
  * state component j alone with g_jj a function of x_j only; dg[j] is

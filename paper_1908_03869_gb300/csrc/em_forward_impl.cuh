@@ -187,7 +187,7 @@ __device__ __forceinline__ void rk4_stage(M &model, const Real (&at)[M::U][P], c
 
 // One step of the classical fourth-order Runge-Kutta method on the drift
 // alone (the ODE path; the paper lists Runge-Kutta among its ODE
-// integrators, Sec. 1.2): stages at x, x + k1/2, x + k2/2, x + k3 with
+// integrators, Sec. 1.5): stages at x, x + k1/2, x + k2/2, x + k3 with
 // k = h f, and (k1 + 2 k2 + 2 k3 + k4) / 6 goes through the same compensated
 // accumulation as an Euler-Maruyama increment.  No noise is drawn.  The
 // stage states are built on the model's stage base (for the phase models
@@ -216,7 +216,7 @@ __device__ __forceinline__ void rk4_step(M &model, Real (&x)[M::U][P], Real (&cp
 constexpr int kNewtonIters = 4;
 
 // One step of an implicit ODE scheme on the drift alone (the paper lists
-// implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.2):
+// implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.5):
 // the increment d solves d = h f(x + theta d) -- theta = 1 implicit Euler,
 // 1/2 implicit midpoint -- by kNewtonIters Newton iterations from d = 0:
 // at z = x + theta d the residual r = h f(z) - d (the model's increment with

@@ -140,7 +140,7 @@ struct KuramotoLane {
 // Milstein correction for diagonal noise whose channel drives one component
 // with g = s x (multiplicative): 1/2 g g' (dW^2 - dt) = 1/2 (s sqrt(dt))^2 x (N^2 - 1).
 // (The Milstein scheme, named by the paper as the next integrator in
-// Sec. 1.3 and Sec. 4; Kloeden and Platen's form for diagonal noise.)
+// Sec. 2.1 and Sec. 3; Kloeden and Platen's form for diagonal noise.)
 template <typename Real>
 __device__ __forceinline__ Real milstein_multiplicative(Real half_gsq2, Real x, Real N) {
     return half_gsq2 * x * (N * N - Real(1));

@@ -1,6 +1,6 @@
 """GPU parity of the implicit ODE schemes (SDEB_FLAG_IMPLICIT_EULER and
 SDEB_FLAG_IMPLICIT_MIDPOINT: implicit Euler and the implicit midpoint rule on
-the drift alone, the paper's ODE integrators of Sec. 1.2) against the
+the drift alone, the paper's ODE integrators of Sec. 1.5) against the
 oracle's pinned implicit step: 4 Newton iterations from the old state, a
 dense LU solve in the oracle, the closed-form structured solve of each model
 (Woodbury for the Kuramoto models, block Sherman-Morrison for the

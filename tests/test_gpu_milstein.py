@@ -1,5 +1,5 @@
 """GPU parity of the Milstein step (SDEB_FLAG_MILSTEIN; the scheme the paper
-names as the next integrator, Sec. 1.3 and Sec. 4) against the oracle's
+names as the next integrator, Sec. 2.1 and Sec. 3) against the oracle's
 pinned Milstein step on the same inputs and the same Philox noise.
 
 * GBM (g = sigma x) and the FitzHugh-Nagumo network (g = sigma v on v):

@@ -1,6 +1,6 @@
 """GPU parity of the ODE path (SDEB_FLAG_RK4: classical fourth-order
 Runge-Kutta on the drift alone; the paper lists Runge-Kutta among its ODE
-integrators, Sec. 1.2) against the oracle's pinned RK4 step.
+integrators, Sec. 1.5) against the oracle's pinned RK4 step.
 
 * Every model: FP64 <= 1e-12 over 400 steps and FP32 <= 1e-4 over 200 steps
   of dt = 0.01 (frames and final state).  Without noise the n = 128

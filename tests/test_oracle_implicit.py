@@ -1,6 +1,6 @@
 """Pins of the oracle's implicit ODE schemes on the drift alone (the paper
 lists implicit Euler and implicit midpoint among its ODE integrators,
-Sec. 1.2), each step solved by a fixed count of Newton iterations:
+Sec. 1.5), each step solved by a fixed count of Newton iterations:
 
 * The drift Jacobian against central differences of the drift, every model.
 * Linear ODE dx/dt = -theta x (closed forms): implicit Euler gives

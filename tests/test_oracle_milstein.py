@@ -1,5 +1,5 @@
 """Pins of the oracle's Milstein step (the scheme the paper names as the
-next one to add, Sec. 1.3 and Sec. 4; Kloeden and Platen, Sec. 10.3), for
+next one to add, Sec. 2.1 and Sec. 3; Kloeden and Platen, Sec. 10.3), for
 diagonal noise: X_j += f_j dt + g_jj dW_j + 1/2 g_jj g_jj' (dW_j^2 - dt).
 
 * The diffusion derivative against central differences of the diffusion.

@@ -1,6 +1,6 @@
 """Pins of the oracle's fourth-order Runge-Kutta step on the drift alone
 (the ODE path: the paper lists Runge-Kutta among its ODE integrators,
-Sec. 1.2; classical RK4):
+Sec. 1.5; classical RK4):
 
 * Linear ODE dx/dt = -theta x: RK4 multiplies x by the degree-4 Taylor
   polynomial of exp(-h theta) every step, so x_K = R(h theta)^K x0 with
