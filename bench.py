@@ -357,6 +357,11 @@ def run_ours(args):
     if not args.no_rk4:
         rk4 = _time_rk4(stream, rank)
 
+    # ---- particle swarm search over the coupling: whole generations on the GPU
+    swarm = None
+    if not args.no_swarm:
+        swarm = _time_swarm(stream, rank)
+
     # ---- a user-defined model compiled at run time, beside the built-in one --
     user = None
     if not args.no_user_model:
@@ -401,7 +406,7 @@ def run_ours(args):
                          "peak_source": "16 SFU results/clk/SM x 152 SMs x 2070 MHz",
                          "ops_per_osc_step": SFU_OPS_PER_OSC_STEP},
             "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "batched": batched, "fhn": fhn, "rk4": rk4,
-            "user_model": user, "paper_speed_protocol": paper, "paper_accuracy_protocol": paper_acc,
+            "user_model": user, "swarm_search": swarm, "paper_speed_protocol": paper, "paper_accuracy_protocol": paper_acc,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": len(CONFIGS) * args.steps,
@@ -647,6 +652,55 @@ def _paper_accuracy_protocol(stream, rank):
     return out
 
 
+def _time_swarm(stream, rank, generations=5, particles=1024, realisations=64, n=32, steps=1000):
+    """Particle swarm search over (K, sigma) of the Kuramoto model: 1024
+    particles x 64 realisations = 2^16 orbits of n = 32, dt = 0.005, 1000
+    steps, FP32, target order parameter 0.8.  A generation is expand +
+    set_params + integrate + read_final + fitness + update on one stream;
+    timed over 5 generations after one untimed one, beside set_params +
+    integrate alone."""
+    import torch
+
+    import paper_1908_03869_gb300 as sdeb
+    from paper_1908_03869_gb300 import inputs
+    from paper_1908_03869_gb300.swarm import SwarmSearch
+
+    p, x0 = inputs.kuramoto(n, realisations, seed=11 + rank)
+    base = p[0].copy()
+    pb = sdeb.Problem.make("kuramoto", n, 1, DT, steps, steps, SEED, "fp32")
+    g = torch.Generator().manual_seed(3 + rank)
+    x_init = torch.rand((particles, 2), generator=g, dtype=torch.float64) * torch.tensor([4.0, 0.5])
+    v_init = torch.zeros((particles, 2), dtype=torch.float64)
+    orbit_steps = particles * realisations * steps
+    out = {"workload": "Kuramoto n = %d, %d particles x %d realisations (%d orbits), dt = %g, %d steps, fp32, "
+                       "search over (K, sigma), target r = 0.8" % (n, particles, realisations,
+                                                                   particles * realisations, DT, steps)}
+    with SwarmSearch(pb, base, x0, [0, 1], [0.0, 0.0], [4.0, 0.5], particles, r_target=0.8, swarm_seed=7) as s:
+        s.reset(x_init, v_init)
+        with torch.cuda.stream(stream):
+            s.step(stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(generations):
+                s.step(stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            gen_ms = a.elapsed_time(b) / generations
+            a.record(stream)
+            for _ in range(generations):
+                s.it.set_params(s.params, s.x0_all, stream=stream)
+                s.it.integrate(stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            integ_ms = a.elapsed_time(b) / generations
+            _, best_fit = s.best()
+    out.update({"ms_per_generation": gen_ms, "orbit_steps_per_sec": orbit_steps / (gen_ms / 1e3),
+                "integration_ms": integ_ms, "integration_share": integ_ms / gen_ms,
+                "best_fitness_after": best_fit, "generations_run": generations + 1})
+    return out
+
+
 def _time_rk4(stream, rank, reps=3, steps=1000):
     """The ODE path: classical fourth-order Runge-Kutta, implicit Euler and
     the implicit midpoint rule (4 Newton iterations a step) on the drift of
@@ -772,6 +826,7 @@ def main():
     ap.add_argument("--no-rk4", action="store_true")
     ap.add_argument("--no-paper-protocol", action="store_true")
     ap.add_argument("--no-user-model", action="store_true")
+    ap.add_argument("--no-swarm", action="store_true")
     ap.add_argument("--orbit-scale", type=float, default=1.0,
                     help="scale the orbit counts (profiling runs only; the benchmark uses 1)")
     ap.add_argument("--horizon", type=int, default=None,

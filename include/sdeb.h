@@ -392,6 +392,54 @@ SDEB_API sdeb_status sdeb_order_param(const void *theta, int64_t orbits, int32_t
 SDEB_API sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void *params, const void *x0,
                                             void *x_final, void *frames, void *stream);
 
+/* ---- Particle swarm search over model parameters ------------------------
+ * The population-based parameter optimisation the paper builds the
+ * integrator for (Sec. 1.2: an EA or a particle swarm integrates the model
+ * over every parameter set of its population each generation, with several
+ * realisations per set against the noise).  A generation is
+ *   sdeb_swarm_expand   particles -> per-orbit parameter rows,
+ *   sdeb_set_params(on_device = 1) + sdeb_integrate   (or the noalloc path),
+ *   sdeb_swarm_fitness  final states -> one fitness per particle,
+ *   sdeb_swarm_update   personal and global bests, velocities, positions,
+ * all asynchronous on one stream, nothing read back in between.  P particles
+ * of D <= SDEB_SWARM_MAX_DIMS dimensions; particle i's realisation q is
+ * orbit i R + q.  Swarm arrays are FP64 device arrays, row-major:
+ * x, v, pbest [P][D], pbest_fit, fit [P].  Host arrays (dims, lo, hi) are
+ * read during the call.  EINVAL on NULL pointers, P < 1, R < 1, D outside
+ * [1, SDEB_SWARM_MAX_DIMS], a column outside [0, d), lo > hi; ECUDA on a
+ * launch error. */
+#define SDEB_SWARM_MAX_DIMS 16
+
+/* params_out[i R + q][c] = x[i][j] where c == dims[j], else base[c]:
+ * base [d] and params_out [P R][d] device, in `precision` (x rounded to
+ * FP32 for SDEB_FP32_KAHAN); dims [D] host, distinct columns. */
+SDEB_API sdeb_status sdeb_swarm_expand(const double *x, int64_t particles, int32_t dims_count,
+                                       const int32_t *dims, const void *base, int32_t d, int32_t realisations,
+                                       int32_t precision, void *params_out, void *stream);
+
+/* fit[i] = (mean over q of r(theta[i R + q]) - r_target)^2 with r the order
+ * parameter of Eq. 7, computed in FP64 from theta [P R][n] (device, in
+ * `precision`); the realisations are summed in a fixed order. */
+SDEB_API sdeb_status sdeb_swarm_fitness(const void *theta, int64_t particles, int32_t realisations, int32_t n,
+                                        int32_t precision, double r_target, double *fit, void *stream);
+
+/* One generation g of the inertia-weight particle swarm (Kennedy and
+ * Eberhart; inertia weight of Shi and Eberhart), minimising the fitness:
+ *   where fit[i] < pbest_fit[i]: pbest[i] = x[i], pbest_fit[i] = fit[i]
+ *     (a NaN fitness never improves; start pbest_fit at +inf);
+ *   b = the least pbest_fit, the lowest index among equals -> *gbest;
+ *   v = w v + c1 r1 (pbest[i] - x[i]) + c2 r2 (pbest[b] - x[i]), clamped
+ *   to +-(hi - lo); x = x + v clamped to [lo, hi], per dimension;
+ * r1, r2 = (w + 1/2) 2^-32 of words 0 and 1 of Philox4x32-10 with key `seed`
+ * and counter (g, j, i, 2) -- the noise generator on counter stream 2.  Each
+ * product and sum is rounded separately, in the order written.  x, v, pbest,
+ * pbest_fit updated in place; fit [P] and gbest (one int32) device; lo, hi
+ * [D] host.  P <= 2^24. */
+SDEB_API sdeb_status sdeb_swarm_update(double *x, double *v, double *pbest, double *pbest_fit, const double *fit,
+                                       int64_t particles, int32_t dims_count, const double *lo, const double *hi,
+                                       double w, double c1, double c2, uint64_t seed, uint32_t generation,
+                                       int32_t *gbest, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

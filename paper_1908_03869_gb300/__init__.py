@@ -27,6 +27,7 @@ __all__ = [
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
     "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
     "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "sdeb_batch_plan", "model_shape",
+    "sdeb_swarm_expand", "sdeb_swarm_fitness", "sdeb_swarm_update", "SDEB_SWARM_MAX_DIMS",
     "EXPORTED_SYMBOLS",
 ]
 
@@ -36,6 +37,7 @@ SDEB_USER_MAX_N = SDEB_USER_MAX_M = 64
 SDEB_FP32_KAHAN, SDEB_FP64 = 0, 1
 SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES, SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4 = 1, 2, 4, 8
 SDEB_FLAG_IMPLICIT_EULER, SDEB_FLAG_IMPLICIT_MIDPOINT = 16, 32
+SDEB_SWARM_MAX_DIMS = 16
 IMPLICIT_FLAGS = {None: 0, "euler": SDEB_FLAG_IMPLICIT_EULER, "midpoint": SDEB_FLAG_IMPLICIT_MIDPOINT}
 
 MODEL_IDS = {
@@ -125,6 +127,12 @@ _SIGS = {
     "sdeb_batch_layout": (_ST, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sdeb_batch_plan": (_ST, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P,
                               _P, ctypes.POINTER(ctypes.c_int32)]),
+    "sdeb_swarm_expand": (_ST, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.c_int32, _P, _P]),
+    "sdeb_swarm_fitness": (_ST, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                 _P, _P]),
+    "sdeb_swarm_update": (_ST, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, _P, _P]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -298,6 +306,29 @@ def sdeb_normals_fill(seed, k0, nk, o0, no, m, precision, out, stream=None):
 
 def sdeb_order_param(theta, orbits, n, precision, r, dr=None, stream=None):
     _check(lib().sdeb_order_param(theta, orbits, n, precision, r, dr, _stream(stream)))
+
+
+def sdeb_swarm_expand(x, particles, dims, base, d, realisations, precision, params_out, stream=None):
+    """dims: a sequence of parameter columns (copied to a host int32 array)."""
+    cols = (ctypes.c_int32 * len(dims))(*dims)
+    _check(lib().sdeb_swarm_expand(x, particles, len(dims), cols, base, d, realisations,
+                                   PRECISIONS.get(precision, precision), params_out, _stream(stream)))
+
+
+def sdeb_swarm_fitness(theta, particles, realisations, n, precision, r_target, fit, stream=None):
+    _check(lib().sdeb_swarm_fitness(theta, particles, realisations, n, PRECISIONS.get(precision, precision),
+                                    float(r_target), fit, _stream(stream)))
+
+
+def sdeb_swarm_update(x, v, pbest, pbest_fit, fit, particles, lo, hi, w, c1, c2, seed, generation, gbest,
+                      stream=None):
+    """lo, hi: sequences of the D bounds (copied to host float64 arrays)."""
+    lo_a = (ctypes.c_double * len(lo))(*[float(t) for t in lo])
+    hi_a = (ctypes.c_double * len(hi))(*[float(t) for t in hi])
+    if len(lo) != len(hi):
+        raise ValueError("lo and hi need one bound per dimension")
+    _check(lib().sdeb_swarm_update(x, v, pbest, pbest_fit, fit, particles, len(lo), lo_a, hi_a, float(w), float(c1),
+                                   float(c2), seed & 0xFFFFFFFFFFFFFFFF, generation, gbest, _stream(stream)))
 
 
 def sdeb_integrate_noalloc(problem, params, x0, x_final, frames=None, stream=None):
