@@ -288,7 +288,7 @@ def run_ours(args):
         def e2e_step():
             for i, it in enumerate(its):
                 stream.wait_event(copied[i])      # the previous step's frames of this problem are out
-                it.set_params(*host_inputs[i], stream=stream)
+                it.set_params(*host_inputs[i], stream=stream, async_host=True)
                 f_done = 0
                 for c in range(E2E_CHUNKS):
                     k0, k1 = c * STEPS // E2E_CHUNKS, (c + 1) * STEPS // E2E_CHUNKS
@@ -298,7 +298,7 @@ def run_ours(args):
                     copy_stream.wait_event(ready)
                     f_end = k1 // STRIDE + 1
                     it.frames(begin=f_done, count=f_end - f_done, out=host_frames[i][f_done:f_end],
-                              stream=copy_stream)
+                              stream=copy_stream, async_host=True)
                     f_done = f_end
                 copied[i].record(copy_stream)
 

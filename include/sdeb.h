@@ -260,10 +260,25 @@ SDEB_API sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source
  * NULL is accepted. */
 SDEB_API void sdeb_destroy(sdeb_ctx *ctx);
 
+/* Where the host-side buffer of a copy call lives (the on_device argument
+ * of sdeb_set_params, the dst_on_device argument of the read calls):
+ *   SDEB_MEM_HOST        host memory; the copy has completed on return;
+ *   SDEB_MEM_DEVICE      device memory; the copy is ordered on `stream`;
+ *   SDEB_MEM_HOST_ASYNC  host memory; the copy is only enqueued on `stream`
+ *                        (it overlaps other streams' work when the buffer is
+ *                        page-locked): keep the buffer alive, and unchanged
+ *                        for an input, until the stream has passed the copy;
+ *                        synchronise before reading an output.
+ * Any other value is EINVAL. */
+#define SDEB_MEM_HOST 0
+#define SDEB_MEM_DEVICE 1
+#define SDEB_MEM_HOST_ASYNC 2
+
 /* Load parameter sets and initial states (Table 2 arguments "params" and
  * "initx").  params: [orbits][d] (or [d] when shared); x0: [orbits][n];
- * element type = context precision.  on_device = 0: host pointers, copied
- * before return; 1: device pointers, copied on `stream`.  Resets the step
+ * element type = context precision.  on_device: SDEB_MEM_* (SDEB_MEM_HOST:
+ * copied before return; SDEB_MEM_DEVICE: copied on `stream`;
+ * SDEB_MEM_HOST_ASYNC: host pointers copied on `stream`).  Resets the step
  * counter to 0 and writes frame 0. */
 SDEB_API sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0,
                             int32_t on_device, void *stream);
@@ -279,12 +294,12 @@ SDEB_API sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_
 
 /* Copy frames [frame_begin, frame_begin + frame_count) into dst, layout
  * [frame_count][orbits][n]; dst_bytes must equal that size exactly.  Frames
- * past the current step are ESTATE.  dst_on_device selects device/host dst
- * (host copies complete before return). */
+ * past the current step are ESTATE.  dst_on_device: SDEB_MEM_*. */
 SDEB_API sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int64_t frame_begin,
                              int64_t frame_count, int32_t dst_on_device, void *stream);
 
-/* Copy the current state [orbits][n] into dst (dst_bytes exact). */
+/* Copy the current state [orbits][n] into dst (dst_bytes exact);
+ * dst_on_device: SDEB_MEM_*. */
 SDEB_API sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t dst_on_device,
                             void *stream);
 

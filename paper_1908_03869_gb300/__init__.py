@@ -28,6 +28,7 @@ __all__ = [
     "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
     "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "sdeb_batch_plan", "model_shape",
     "sdeb_swarm_expand", "sdeb_swarm_fitness", "sdeb_swarm_update", "SDEB_SWARM_MAX_DIMS",
+    "SDEB_MEM_HOST", "SDEB_MEM_DEVICE", "SDEB_MEM_HOST_ASYNC",
     "EXPORTED_SYMBOLS",
 ]
 
@@ -38,6 +39,7 @@ SDEB_FP32_KAHAN, SDEB_FP64 = 0, 1
 SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES, SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4 = 1, 2, 4, 8
 SDEB_FLAG_IMPLICIT_EULER, SDEB_FLAG_IMPLICIT_MIDPOINT = 16, 32
 SDEB_SWARM_MAX_DIMS = 16
+SDEB_MEM_HOST, SDEB_MEM_DEVICE, SDEB_MEM_HOST_ASYNC = 0, 1, 2
 IMPLICIT_FLAGS = {None: 0, "euler": SDEB_FLAG_IMPLICIT_EULER, "midpoint": SDEB_FLAG_IMPLICIT_MIDPOINT}
 
 MODEL_IDS = {

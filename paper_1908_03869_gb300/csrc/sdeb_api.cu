@@ -700,19 +700,32 @@ void sdeb_destroy(sdeb_ctx *ctx) {
     delete ctx;
 }
 
+// Memory kinds of the copy calls' host-side buffers (SDEB_MEM_*).
+static bool mem_kind_valid(int32_t k) { return k == SDEB_MEM_HOST || k == SDEB_MEM_DEVICE || k == SDEB_MEM_HOST_ASYNC; }
+
+// The copy of a read call to dst (SDEB_MEM_*): device to device, or to host
+// memory, waited for unless SDEB_MEM_HOST_ASYNC.
+static cudaError_t read_copy(void *dst, const void *src, size_t bytes, int32_t dst_kind, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes,
+                                    dst_kind == SDEB_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dst_kind == SDEB_MEM_HOST) e = cudaStreamSynchronize(s);
+    return e;
+}
+
 sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0, int32_t on_device,
                             void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (!params || !x0) return fail(ctx, SDEB_EINVAL, "params and x0 must not be NULL");
+    if (!mem_kind_valid(on_device)) return fail(ctx, SDEB_EINVAL, "on_device %d is not SDEB_MEM_*", on_device);
     const cudaStream_t s = as_stream(stream);
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kind = on_device == SDEB_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (ctx->is_batch) {
         const size_t sb = (size_t)ctx->batch_state_elems * ctx->elem;
         cudaError_t e = cudaMemcpyAsync(ctx->d_params, params, (size_t)ctx->batch_params_bytes, kind, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_x, x0, sb, kind, s);
         if (e == cudaSuccess && ctx->d_comp) e = cudaMemsetAsync(ctx->d_comp, 0, (size_t)ctx->batch_state_elems * 4, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flags, 0, (size_t)ctx->batch_items, s);
-        if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && on_device == SDEB_MEM_HOST) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             ctx->params_set = false;
@@ -733,7 +746,7 @@ sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0, i
         e = cudaMemcpyAsync(ctx->d_ckpt, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && ctx->d_ckpt_comp) e = cudaMemsetAsync(ctx->d_ckpt_comp, 0, state_bytes, s);
     if (e == cudaSuccess && ctx->d_flags) e = cudaMemsetAsync(ctx->d_flags, 0, (size_t)ctx->pb.orbits, s);
-    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && on_device == SDEB_MEM_HOST) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ctx->params_set = false;
@@ -822,6 +835,7 @@ sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int64_t
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "use sdeb_batch_read on a batch");
     if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
+    if (!mem_kind_valid(dst_on_device)) return fail(ctx, SDEB_EINVAL, "dst_on_device %d is not SDEB_MEM_*", dst_on_device);
     if (!ctx->d_frames) return fail(ctx, SDEB_ESTATE, "context was created without frames");
     if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
     if (frame_begin < 0 || frame_count < 0 || frame_begin + frame_count > ctx->nframes)
@@ -835,9 +849,8 @@ sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int64_t
         return fail(ctx, SDEB_EINVAL, "dst_bytes=%zu, expected %zu", dst_bytes, frame_bytes * (size_t)frame_count);
     if (frame_count == 0) return SDEB_OK;
     const cudaStream_t s = as_stream(stream);
-    cudaError_t e = cudaMemcpyAsync(dst, static_cast<char *>(ctx->d_frames) + frame_bytes * frame_begin,
-                                    dst_bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(s);
+    cudaError_t e = read_copy(dst, static_cast<char *>(ctx->d_frames) + frame_bytes * frame_begin, dst_bytes,
+                              dst_on_device, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(ctx, e, "sdeb_read_orbits copy");
@@ -849,13 +862,12 @@ sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t 
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "use sdeb_batch_read on a batch");
     if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
+    if (!mem_kind_valid(dst_on_device)) return fail(ctx, SDEB_EINVAL, "dst_on_device %d is not SDEB_MEM_*", dst_on_device);
     if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
     const size_t bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
     if (dst_bytes != bytes) return fail(ctx, SDEB_EINVAL, "dst_bytes=%zu, expected %zu", dst_bytes, bytes);
     const cudaStream_t s = as_stream(stream);
-    cudaError_t e = cudaMemcpyAsync(dst, ctx->d_x, bytes,
-                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(s);
+    cudaError_t e = read_copy(dst, ctx->d_x, bytes, dst_on_device, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(ctx, e, "sdeb_read_final copy");
@@ -1135,6 +1147,7 @@ sdeb_status sdeb_batch_read(sdeb_ctx *ctx, int32_t instance, int32_t what, void 
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (!ctx->is_batch) return fail(ctx, SDEB_EINVAL, "not a batch context");
     if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");
+    if (!mem_kind_valid(dst_on_device)) return fail(ctx, SDEB_EINVAL, "dst_on_device %d is not SDEB_MEM_*", dst_on_device);
     if (instance < 0 || instance >= (int32_t)ctx->inst.size())
         return fail(ctx, SDEB_EINVAL, "instance %d outside [0, %d)", instance, (int)ctx->inst.size());
     if (!ctx->batch_done) return fail(ctx, SDEB_ESTATE, "integrate the batch first");
@@ -1153,8 +1166,7 @@ sdeb_status sdeb_batch_read(sdeb_ctx *ctx, int32_t instance, int32_t what, void 
     }
     if (dst_bytes != bytes) return fail(ctx, SDEB_EINVAL, "dst_bytes=%zu, expected %zu", dst_bytes, bytes);
     const cudaStream_t s = as_stream(stream);
-    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && !dst_on_device) e = cudaStreamSynchronize(s);
+    cudaError_t e = read_copy(dst, src, bytes, dst_on_device, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(ctx, e, "sdeb_batch_read copy");

@@ -8,13 +8,21 @@ import ctypes
 
 import torch
 
-from . import (SDEB_FLAG_NO_FRAMES, SDEB_FLAG_SHARED_PARAMS, SDEB_FP64, Problem, sdeb_autotune, sdeb_create,
+from . import (SDEB_FLAG_NO_FRAMES, SDEB_FLAG_SHARED_PARAMS, SDEB_FP64, SDEB_MEM_DEVICE, SDEB_MEM_HOST,
+               SDEB_MEM_HOST_ASYNC, Problem, sdeb_autotune, sdeb_create,
                sdeb_destroy, sdeb_get_layout, sdeb_grad, sdeb_integrate, sdeb_integrate_range, sdeb_orbit_flags,
                sdeb_read_final, sdeb_read_orbits, sdeb_set_layout, sdeb_set_params)
 
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _mem(t, async_host):
+    """SDEB_MEM_* of tensor t: device, or host waited for / only enqueued."""
+    if t.is_cuda:
+        return SDEB_MEM_DEVICE
+    return SDEB_MEM_HOST_ASYNC if async_host else SDEB_MEM_HOST
 
 
 class Integrator:
@@ -57,7 +65,10 @@ class Integrator:
             return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
         return getattr(stream, "cuda_stream", stream)
 
-    def set_params(self, params: torch.Tensor, x0: torch.Tensor, stream=None):
+    def set_params(self, params: torch.Tensor, x0: torch.Tensor, stream=None, async_host=False):
+        """async_host: host tensors are only enqueued for copying on the
+        stream (page-locked ones overlap other streams); they must stay
+        unchanged until the stream has passed the copy."""
         pb = self.pb
         want_p = (pb.d,) if self.shared else (pb.orbits, pb.d)
         if tuple(params.shape) != want_p or tuple(x0.shape) != (pb.orbits, pb.n):
@@ -69,7 +80,7 @@ class Integrator:
             raise ValueError("params and x0 must both be host or both be device tensors")
         params, x0 = params.contiguous(), x0.contiguous()
         self._keep = (params, x0)  # device copies are stream-ordered: keep the sources alive
-        sdeb_set_params(self.ctx, _ptr(params), _ptr(x0), params.is_cuda, self._stream(stream))
+        sdeb_set_params(self.ctx, _ptr(params), _ptr(x0), _mem(params, async_host), self._stream(stream))
 
     def set_layout(self, lanes_per_orbit, units_per_lane):
         sdeb_set_layout(self.ctx, lanes_per_orbit, units_per_lane)
@@ -88,20 +99,23 @@ class Integrator:
     def integrate_range(self, k_begin, k_end, stream=None):
         sdeb_integrate_range(self.ctx, k_begin, k_end, self._stream(stream))
 
-    def frames(self, begin=0, count=None, device="cuda", stream=None, out=None):
+    def frames(self, begin=0, count=None, device="cuda", stream=None, out=None, async_host=False):
+        """async_host: a host `out` is only enqueued on the stream;
+        synchronise before reading it."""
         count = self.nframes - begin if count is None else count
         shape = (count, self.pb.orbits, self.pb.n)
         if out is None:
             out = torch.empty(shape, dtype=self.dtype, device=device,
                               pin_memory=(device == "cpu" and torch.cuda.is_available()))
-        sdeb_read_orbits(self.ctx, _ptr(out), out.numel() * out.element_size(), begin, count, out.is_cuda,
-                         self._stream(stream))
+        sdeb_read_orbits(self.ctx, _ptr(out), out.numel() * out.element_size(), begin, count,
+                         _mem(out, async_host), self._stream(stream))
         return out
 
-    def final(self, device="cuda", stream=None, out=None):
+    def final(self, device="cuda", stream=None, out=None, async_host=False):
         if out is None:
             out = torch.empty((self.pb.orbits, self.pb.n), dtype=self.dtype, device=device)
-        sdeb_read_final(self.ctx, _ptr(out), out.numel() * out.element_size(), out.is_cuda, self._stream(stream))
+        sdeb_read_final(self.ctx, _ptr(out), out.numel() * out.element_size(), _mem(out, async_host),
+                        self._stream(stream))
         return out
 
     def flags(self, stream=None):
