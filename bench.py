@@ -143,8 +143,9 @@ def _cpu_sample(nthreads, budget_orbits):
 
 
 def _sample_sizes(cores):
-    # about 3-10 s of CPU work per problem on `cores` threads
-    return [8 * cores, 2 * cores, max(1, cores // 4)]
+    # 2-3 s per problem on `cores` threads, every thread busy (at least one
+    # orbit per thread for each problem): about 8 s for the three
+    return [320 * cores, 30 * cores, cores]
 
 
 def run_reference(args):
