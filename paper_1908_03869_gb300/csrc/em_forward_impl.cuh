@@ -162,7 +162,7 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
 
 // One stage of the classical fourth-order Runge-Kutta step (below): the
 // coupling sums at the stage state `at`, then per unit the
-// model's increment with a zero normal, h f(at); acc += weight h f(at), and
+// model's drift increment h f(at); acc += weight h f(at), and
 // y = base + frac_next h f(at) is the next stage's state (y may be `at`:
 // each unit is read before it is overwritten, the sums were taken first).
 template <class M, typename Real, int P, class RED>
@@ -176,7 +176,7 @@ __device__ __forceinline__ void rk4_stage(M &model, const Real (&at)[M::U][P], c
 #pragma unroll
     for (int i = 0; i < P; ++i) {
         Real inc[M::U];
-        model.incr(i, at, red, Real(0), inc);
+        model.drift_incr(i, at, red, inc);
 #pragma unroll
         for (int c = 0; c < M::U; ++c) {
             acc[c][i] = fma_r(weight, inc[c], acc[c][i]);
@@ -219,8 +219,8 @@ constexpr int kNewtonIters = 4;
 // implicit Euler and implicit midpoint among its ODE integrators, Sec. 1.5):
 // the increment d solves d = h f(x + theta d) -- theta = 1 implicit Euler,
 // 1/2 implicit midpoint -- by kNewtonIters Newton iterations from d = 0:
-// at z = x + theta d the residual r = h f(z) - d (the model's increment with
-// a zero normal), then d += (I - theta h J(z))^-1 r, the solve done by the
+// at z = x + theta d the residual r = h f(z) - d (the model's drift
+// increment), then d += (I - theta h J(z))^-1 r, the solve done by the
 // model in closed form for its Jacobian's structure.  d then goes through
 // the compensated accumulation.  No noise is drawn.  z is built on the
 // model's stage base, as the Runge-Kutta stages are.
@@ -247,7 +247,7 @@ __device__ __forceinline__ void implicit_step(M &model, Real (&x)[M::U][P], Real
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             Real inc[M::U];
-            model.incr(i, z, red, Real(0), inc);
+            model.drift_incr(i, z, red, inc);
 #pragma unroll
             for (int c = 0; c < M::U; ++c) r[c][i] = inc[c] - d[c][i];
         }

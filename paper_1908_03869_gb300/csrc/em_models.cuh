@@ -18,6 +18,7 @@
 //   incr(i, x, red, N, inc)           the Eq. 2 increment f dt + g sqrt(dt) N
 //                                     of unit i's components, after red has
 //                                     been summed over the G lanes.
+//   drift_incr(i, x, red, inc)        f dt alone (the ODE schemes' stages)
 //   newton_solve(z, red, r, theta,    r <- (I - theta dt J(z))^-1 r for the
 //                u0, units, reduce)   implicit ODE schemes, J the drift's
 //                                     Jacobian, after prepare(z) and the sums
@@ -102,38 +103,44 @@ struct KuramotoLane {
         inc[0] = fma_r(kn_dt, coupling, fma_r(gsq[PAPER ? i : 0], N, omega_dt[i]));
     }
 
+    __device__ __forceinline__ void drift_incr(int i, const Real (&)[U][P], const Real (&red)[NR],
+                                               Real (&inc)[U]) const {
+        inc[0] = fma_r(kn_dt, fma_r(red[1], cs[i], -mul_r(red[0], sn[i])), omega_dt[i]);
+    }
+
     // With c_i = cos z_i, s_i = sin z_i the drift's Jacobian is
     // (K/n) (c c^T + s s^T) - diag((K/n) (C c_i + S s_i)), so
     // I - theta dt J = D - beta U U^T with U = [c s], beta = theta (K/n) dt,
     // D = diag(1 + beta (C c_i + S s_i)): solved by the Woodbury identity,
     // w = D^-1 r, m = U^T D^-1 U and q = U^T w summed over the orbit's units,
-    // r <- w + beta D^-1 U (I - beta m)^-1 q.  D is nonsingular while
-    // theta K dt < 1.  Padding units get a zero correction.
+    // r <- w + beta D^-1 U (I - beta m)^-1 q.  m22 = sum s^2 / a is taken as
+    // sum 1 / a - m11 (c^2 + s^2 = 1).  D is nonsingular while theta K dt < 1.
+    // Padding units get a zero correction.
     template <class RED>
     __device__ __forceinline__ void newton_solve(const Real (&)[U][P], const Real (&red)[NR], Real (&r)[U][P],
                                                  Real theta, int, int, RED &reduce) const {
         const Real C = red[0], S = red[1], beta = theta * kn_dt;
-        Real inv_a[P], m[2] = {Real(0), Real(0)}, q[2] = {Real(0), Real(0)}, m22[1] = {Real(0)};
+        Real inv_a[P], m[2] = {Real(0), Real(0)}, q[2] = {Real(0), Real(0)}, ia[1] = {Real(0)};
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             inv_a[i] = live[i] * recip_fast(fma_r(beta, fma_r(C, cs[i], mul_r(S, sn[i])), Real(1)));
             const Real w = r[0][i] * inv_a[i];
-            const Real tc = cs[i] * inv_a[i], ts = sn[i] * inv_a[i];
+            const Real tc = cs[i] * inv_a[i];
             r[0][i] = w;
             m[0] = fma_r(cs[i], tc, m[0]);
             m[1] = fma_r(sn[i], tc, m[1]);
-            m22[0] = fma_r(sn[i], ts, m22[0]);
+            ia[0] += inv_a[i];
             q[0] = fma_r(cs[i], w, q[0]);
             q[1] = fma_r(sn[i], w, q[1]);
         }
         reduce(m);
         reduce(q);
-        reduce(m22);
-        const Real e11 = Real(1) - beta * m[0], e22 = Real(1) - beta * m22[0], e12 = -beta * m[1];
-        const Real inv_det = recip_fast(e11 * e22 - e12 * e12);
-        const Real z1 = (e22 * q[0] - e12 * q[1]) * inv_det, z2 = (e11 * q[1] - e12 * q[0]) * inv_det;
+        reduce(ia);
+        const Real e11 = Real(1) - beta * m[0], e22 = Real(1) - beta * (ia[0] - m[0]), e12 = -beta * m[1];
+        const Real b_det = beta * recip_fast(e11 * e22 - e12 * e12);
+        const Real z1 = (e22 * q[0] - e12 * q[1]) * b_det, z2 = (e11 * q[1] - e12 * q[0]) * b_det;
 #pragma unroll
-        for (int i = 0; i < P; ++i) r[0][i] = fma_r(beta * inv_a[i], fma_r(cs[i], z1, sn[i] * z2), r[0][i]);
+        for (int i = 0; i < P; ++i) r[0][i] = fma_r(inv_a[i], fma_r(cs[i], z1, sn[i] * z2), r[0][i]);
     }
 };
 
@@ -200,6 +207,14 @@ struct FhnLane {
         inc[0] = fv * dt + gsq * v * N;
         if constexpr (MIL) inc[0] += milstein_multiplicative(half_gsq2, v, N);
         inc[1] = fw * dt;
+    }
+
+    __device__ __forceinline__ void drift_incr(int i, const Real (&x)[U][P], const Real (&red)[NR],
+                                               Real (&inc)[U]) const {
+        Real v = x[0][i], w = x[1][i];
+        Real mean_v = red[0] * inv_units;
+        inc[0] = (v - v * v * v * Real(1.0 / 3.0) - w + I + c * mean_v - c * v) * dt;
+        inc[1] = eps * (v + a - b * w) * dt;
     }
 
     // I - theta dt J is block diagonal, E_i = [[1 - th (1 - v_i^2 - c), th],
@@ -278,6 +293,11 @@ struct ScalarLane {
             if constexpr (MIL) inc[0] += milstein_multiplicative(half_gsq2, xi, N);
         }
         if (KIND == 2) inc[0] = -rate * xi * dt;
+    }
+
+    __device__ __forceinline__ void drift_incr(int i, const Real (&x)[U][P], const Real (&)[NR > 0 ? NR : 1],
+                                               Real (&inc)[U]) const {
+        inc[0] = (KIND == 1 ? rate : -rate) * x[0][i] * dt;
     }
 
     // The drift is lambda x (lambda = rate for GBM, -rate otherwise):

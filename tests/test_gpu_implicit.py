@@ -14,7 +14,9 @@ agree to rounding whether or not Newton has converged.
   rounding (2.2e-16 relative), departs by 4.2e-13 at t = 3 and 1.9e-11 at
   t = 4 under implicit Euler, so their FP64 horizon is 300 steps.
 * Large steps (dt = 0.2, K dt up to 0.8 for the Kuramoto orbits): FP64
-  <= 1e-12 over 50 steps, where Newton's later iterates matter.
+  <= 1e-12 over 30 steps, where Newton's later iterates matter.  The
+  near-critical orbits are sensitive: the oracle itself, with x0 perturbed
+  by one rounding, departs by up to 4e-13 at t = 6 and 2.5e-12 at t = 10.
 * Every lane layout that covers an n = 32 orbit gives the oracle's orbit.
 * A stiff linear ODE (rate dt = 5): the closed forms (1 + h rate)^-k and
   ((1 - h rate / 2) / (1 + h rate / 2))^k, where Euler-Maruyama diverges.
@@ -90,8 +92,8 @@ def test_implicit_large_steps_match_oracle(scheme, model, n):
     p, x0 = _inputs(model, n, orbits)
     if model == "kuramoto":
         p[:, 0] = np.linspace(0.0, 4.0, orbits)     # K dt up to 0.8
-    fr, fin = _implicit(scheme, model, n, p, x0, "fp64", dt=0.2, steps=50, stride=10)
-    rfr, rfin = run_oracle(model, n, p, x0, 0.2, 50, 10, seed=2, orbit_offset=3, implicit=scheme)
+    fr, fin = _implicit(scheme, model, n, p, x0, "fp64", dt=0.2, steps=30, stride=10)
+    rfr, rfin = run_oracle(model, n, p, x0, 0.2, 30, 10, seed=2, orbit_offset=3, implicit=scheme)
     assert max_rel_err(fr, rfr) < 1e-12
     assert max_rel_err(fin, rfin) < 1e-12
 
