@@ -169,3 +169,19 @@ def test_implicit_errors():
     with pytest.raises(sdeb.SdebError) as e:
         sdeb.sdeb_create_batch([sdeb.Problem.make("kuramoto", 8, 1, 0.01, 10, 1, 1, "fp32", implicit="euler")])
     assert e.value.status == sdeb.SDEB_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("model,n,orbits,steps", [("kuramoto", 1, 5, 50), ("kuramoto", 2, 1, 50),
+                                                  ("kuramoto", 33, 7, 40), ("fhn_net", 2, 3, 50),
+                                                  ("kuramoto", 8, 4, 0)])
+def test_implicit_edge_shapes(scheme, model, n, orbits, steps):
+    """One oscillator (the coupling vanishes), one orbit, a ragged n = 33
+    (a lane with one live unit), one FHN unit, and no steps at all."""
+    p, x0 = _inputs(model, n, orbits)
+    fr, fin = _implicit(scheme, model, n, p, x0, "fp64", steps=steps, stride=10)
+    rfr, rfin = run_oracle(model, n, p, x0, 0.01, steps, 10, seed=2, orbit_offset=3, implicit=scheme)
+    assert max_rel_err(fr, rfr) < 1e-12
+    assert max_rel_err(fin, rfin) < 1e-12
+    if steps == 0:
+        np.testing.assert_array_equal(fin, x0)

@@ -168,3 +168,18 @@ def test_search_fp32_properties():
     _, fin = oracle.integrate(opb, params, x0, orbit_begin=b * R, frames=False)
     ref = oswarm.fitness(fin, 1, R, 0.9)[0]
     assert abs(ref - fbest) < 1e-4
+
+
+def test_single_particle_single_realisation():
+    """P = R = D = 1: the particle is its own global best; its cognitive and
+    social pulls coincide."""
+    from paper_1908_03869_gb300.swarm import SwarmSearch
+    pb, opb, base, x0 = _search_problem("fp64", R=1, steps=100)
+    hist = oswarm.search(opb, base, x0, [0], [0.0], [4.0], [[1.5]], [[0.3]], 4, W, C1, C2, 8, 0.5)
+    with SwarmSearch(pb, base, x0, [0], [0.0], [4.0], 1, W, C1, C2, r_target=0.5, swarm_seed=8) as s:
+        s.reset([[1.5]], [[0.3]])
+        for gen in range(4):
+            s.step()
+            assert int(s.gbest.item()) == 0
+            np.testing.assert_array_equal(s.x.cpu().numpy(), hist[gen]["x"])
+            np.testing.assert_array_equal(s.v.cpu().numpy(), hist[gen]["v"])
