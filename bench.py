@@ -116,10 +116,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_sample(nthreads, budget_orbits):
-    """Oracle (pairwise Kuramoto drift, as it stands) on the first orbits of
-    each problem, full horizon.  Returns (orbit-steps/s over the workload mix,
-    description)."""
+def _cpu_sample(nthreads, budget_orbits, mean_field=False):
+    """Oracle (pairwise Kuramoto drift by definition, as it stands; or its
+    mean-field form) on the first orbits of each problem, full horizon.
+    Returns (orbit-steps/s over the workload mix, description)."""
     import numpy as np
 
     import oracle
@@ -129,7 +129,7 @@ def _cpu_sample(nthreads, budget_orbits):
     desc = []
     for (n, orbits), s in zip(CONFIGS, budget_orbits):
         p, x0 = inputs.kuramoto(n, s, seed=1)
-        pb = oracle.make_problem("kuramoto", n, n, n + 2, DT, STEPS, STRIDE, SEED)
+        pb = oracle.make_problem("kuramoto", n, n, n + 2, DT, STEPS, STRIDE, SEED, mean_field=mean_field)
         t0 = time.perf_counter()
         oracle.integrate(pb, p.astype(np.float32).astype(np.float64), x0.astype(np.float32).astype(np.float64),
                          frames=True, nthreads=nthreads)
@@ -383,9 +383,15 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        v, desc = _cpu_sample(cores, _sample_sizes(cores))
+        sizes = _sample_sizes(cores)
+        v, desc = _cpu_sample(cores, sizes)
+        v1, desc1 = _cpu_sample(1, [max(1, s // cores) for s in sizes])
+        vmf, descmf = _cpu_sample(cores, sizes, mean_field=True)
         cpu = {"value": v, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle",
-               "sample": desc + "; rate scaled to the workload's orbit mix"}
+               "sample": desc + "; rate scaled to the workload's orbit mix",
+               "single_thread": {"value": v1, "cores": 1, "sample": desc1},
+               "mean_field_form": {"value": vmf, "cores": cores, "sample": descmf,
+                                   "note": "the oracle's O(n) mean-field drift instead of the pairwise definition"}}
 
     for it in its:
         it.close()
