@@ -370,11 +370,13 @@ __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const Forward
 // The same kernel with registers capped so that five blocks fit per SM: used
 // for FP32 one-component models on multi-lane layouts with up to 8 units per
 // lane, which fit 96 registers without spilling and ran 2-3 % faster than at
-// the compiler's choice (128 registers, four blocks).  The single-lane
-// layouts keep the compiler's choice (96 registers already).
-template <class M, typename Real, int G, int P>
+// the compiler's choice (128 registers, four blocks).  The implicit schemes
+// use it too (a few spilled words, 1 % faster than four blocks); Runge-Kutta
+// fits 96 registers by itself.  The single-lane layouts keep the compiler's
+// choice (96 registers already).
+template <class M, typename Real, int G, int P, int SCHEME>
 __global__ void __launch_bounds__(kForwardBlock, 5) em_forward_kernel_5blocks(const ForwardArgs a) {
-    em_forward_body<M, Real, G, P, kSchemeEm>(a);
+    em_forward_body<M, Real, G, P, SCHEME>(a);
 }
 
 template <class M, typename Real, int G, int P>
@@ -388,8 +390,8 @@ cudaError_t launch_forward_layout(const ForwardArgs &a, cudaStream_t s) {
     const int64_t threads = a.orbits * G;
     const int64_t grid = (threads + kForwardBlock - 1) / kForwardBlock;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if constexpr (SCHEME == kSchemeEm && kForwardFiveBlocks<M, Real, G, P>)
-        em_forward_kernel_5blocks<M, Real, G, P><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
+    if constexpr ((SCHEME == kSchemeEm || SCHEME == kSchemeImplicit) && kForwardFiveBlocks<M, Real, G, P>)
+        em_forward_kernel_5blocks<M, Real, G, P, SCHEME><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     else
         em_forward_kernel<M, Real, G, P, SCHEME><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     return cudaGetLastError();
