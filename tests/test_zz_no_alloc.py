@@ -72,11 +72,34 @@ def test_noalloc_other_model_without_frames():
         assert max_rel_err(fin, ref_fin) < TOL["fp32"]
 
 
+@pytest.mark.parametrize("scheme", [dict(rk4=True), dict(implicit="euler"), dict(implicit="midpoint"),
+                                    dict(milstein=True)])
+def test_noalloc_step_schemes_match_the_context_api(scheme):
+    """The scheme flags reach the same kernels through this entry point."""
+    model = "gbm" if "milstein" in scheme else "kuramoto"
+    n, orbits, dt, steps, stride = (8, 700, 0.01, 200, 20)
+    if model == "gbm":
+        p, x0 = inputs.scalar_model(n, orbits, [0.3, 0.3], 0.5, 1.5, seed=5)
+    else:
+        p, x0 = inputs.kuramoto(n, orbits, seed=6)
+    p, x0 = p.astype(np.float64), x0.astype(np.float64)
+    ref_fr, ref_fin = run_gpu(model, n, p, x0, dt, steps, stride, seed=2, precision="fp64", **scheme)
+    pb = sdeb.Problem.make(model, n, orbits, dt, steps, stride, 2, "fp64", **scheme)
+    fr, fin = _noalloc(pb, p, x0)
+    assert max_rel_err(fr, ref_fr) < TOL["fp64"]
+    assert max_rel_err(fin, ref_fin) < TOL["fp64"]
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit():
+    L = sdeb.lib()
+    pb = sdeb.Problem.make("kuramoto", 8, 16, 0.01, 10, 10, 0, "fp32", rk4=True)
+    pb.flags |= sdeb.SDEB_FLAG_IMPLICIT_EULER                   # two step schemes
+    st = L.sdeb_integrate_noalloc(ctypes.byref(pb), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                  ctypes.c_void_p(16), None, None)
+    assert st == sdeb.SDEB_EINVAL
     n = 64
     orbits = (1 << 21) // n + 1        # one orbit past the scratch limit
     pb = sdeb.Problem.make("kuramoto", n, orbits, 0.01, 10, 10, 0, "fp32")
-    L = sdeb.lib()
     st = L.sdeb_integrate_noalloc(ctypes.byref(pb), ctypes.c_void_p(16), ctypes.c_void_p(16),
                                   ctypes.c_void_p(16), None, None)
     assert st == sdeb.SDEB_EINVAL
