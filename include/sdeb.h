@@ -256,6 +256,13 @@ SDEB_API sdeb_status sdeb_batch_plan(const sdeb_problem *pbs, int32_t count, dou
  * be loaded; ECUDA when the compiled kernel cannot be loaded on the device. */
 SDEB_API sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source, sdeb_ctx **out);
 
+/* Failure-detection tests inject faults on the host through the environment
+ * variable SDEB_FAULT, read once per process: "alloc:<k>" makes the k-th
+ * allocation of a context's buffers (counted from 0) fail, so sdeb_create
+ * returns SDEB_ENOMEM; "launch:<k>" makes the k-th forward launch fail
+ * without launching, so the integrate call returns SDEB_ECUDA with the step
+ * counter unchanged.  Unset or any other value: no injection. */
+
 /* Free the context and its device buffers (synchronises the device first).
  * NULL is accepted. */
 SDEB_API void sdeb_destroy(sdeb_ctx *ctx);

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <new>
 #include <string>
 #include <vector>
@@ -80,6 +82,38 @@ sdeb_status cuda_fail(sdeb_ctx *ctx, cudaError_t e, const char *what) {
 }
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+// Host-side fault injection for failure-detection tests, nothing on the
+// device: SDEB_FAULT="alloc:<k>" makes the k-th allocation of a context's
+// buffers in this process (counted from 0) fail as out of memory,
+// "launch:<k>" makes the k-th forward launch fail without launching.  Read
+// once, at the first allocation or launch; any other value injects nothing.
+struct FaultPlan {
+    long alloc_at = -1, launch_at = -1;
+    std::atomic<long> allocs{0}, launches{0};
+    FaultPlan() {
+        const char *v = std::getenv("SDEB_FAULT");
+        if (!v) return;
+        long k = -1;
+        if (std::sscanf(v, "alloc:%ld", &k) == 1 && k >= 0) alloc_at = k;
+        else if (std::sscanf(v, "launch:%ld", &k) == 1 && k >= 0) launch_at = k;
+    }
+};
+
+FaultPlan &fault_plan() {
+    static FaultPlan plan;
+    return plan;
+}
+
+bool inject_alloc_fault() {
+    FaultPlan &f = fault_plan();
+    return f.alloc_at >= 0 && f.allocs.fetch_add(1) == f.alloc_at;
+}
+
+bool inject_launch_fault() {
+    FaultPlan &f = fault_plan();
+    return f.launch_at >= 0 && f.launches.fetch_add(1) == f.launch_at;
+}
 
 bool model_shape(int32_t model, int32_t n, int32_t &m, int32_t &d, int32_t &units) {
     switch (model) {
@@ -191,6 +225,7 @@ bool layout_instantiated(int32_t model, Layout l) {
 }
 
 cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream_t s) {
+    if (inject_launch_fault()) return cudaErrorLaunchFailure;
     return launch_forward_any(a, l, fp64, s);
 }
 
@@ -672,7 +707,7 @@ sdeb_status create_context(const sdeb_problem *pb, int32_t units, sdeb_ctx **out
     };
     for (auto &a : allocs) {
         if (a.bytes == 0) continue;
-        e = cudaMalloc(a.p, a.bytes);
+        e = inject_alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc(a.p, a.bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             sdeb_status s = cuda_fail(nullptr, e, a.what);
