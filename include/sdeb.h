@@ -259,9 +259,11 @@ SDEB_API sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source
 /* Failure-detection tests inject faults on the host through the environment
  * variable SDEB_FAULT, read once per process: "alloc:<k>" makes the k-th
  * allocation of a context's buffers (counted from 0) fail, so sdeb_create
- * returns SDEB_ENOMEM; "launch:<k>" makes the k-th forward launch fail
- * without launching, so the integrate call returns SDEB_ECUDA with the step
- * counter unchanged.  Unset or any other value: no injection. */
+ * returns SDEB_ENOMEM; "launch:<k>" makes the k-th forward launch of an
+ * integrate call (sdeb_integrate, sdeb_integrate_range; counted from 0 over
+ * the process, sdeb_autotune's trial launches not counted) fail without
+ * launching, so the integrate call returns SDEB_ECUDA with the step counter
+ * unchanged.  Unset or any other value: no injection. */
 
 /* Free the context and its device buffers (synchronises the device first).
  * NULL is accepted. */
@@ -393,7 +395,10 @@ SDEB_API sdeb_status sdeb_order_param(const void *theta, int64_t orbits, int32_t
  *
  * Semantics are those of sdeb_create + sdeb_set_params(on_device = 1) +
  * sdeb_integrate + reading the frames and the final state, for the same
- * problem: the same kernel produces the same numbers.
+ * problem, with the context at the layout sdeb_create picks: the same kernel
+ * at the same layout produces the same bits.  (A context retuned by
+ * sdeb_autotune or sdeb_set_layout sums the coupling terms in another order
+ * and agrees within the FP32 / FP64 parity tolerances, not bit for bit.)
  *   pb       problem; ckpt_every must be 0; orbits <= SDEB_NOALLOC_MAX_ORBITS
  *            and orbits * n <= SDEB_NOALLOC_MAX_STATES, else SDEB_EINVAL.
  *   params   device, [orbits][d] (or [d] with SDEB_FLAG_SHARED_PARAMS).
@@ -403,8 +408,11 @@ SDEB_API sdeb_status sdeb_order_param(const void *theta, int64_t orbits, int32_t
  *   frames   device, [steps/stride + 1][orbits][n], or NULL for no frames.
  * Element type is the problem precision.  Asynchronous on `stream`.
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Calls share the scratch and it keeps the last
+ * (cudaGetSymbolAddress, with that device current) and remembers it with the
+ * identity of the CUDA context; a call in a different context of the device
+ * (after cudaDeviceReset, or the primary context released and re-created)
+ * looks it up again.  Make a call that looks up -- the first one on a device,
+ * and the first after its context changed -- before any stream capture.  Calls share the scratch and it keeps the last
  * call's contents (each call clears what must start at zero): calls whose
  * work overlaps on the GPU race, so serialise them (one stream, or events).
  * Non-finite orbits are not reported on this path. */

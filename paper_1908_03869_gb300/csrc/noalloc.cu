@@ -16,11 +16,16 @@
 // GPU that loads the library holds it until the process exits.  Host code
 // cannot use the array's name as a device address (on the host that name
 // is only a stand-in), so the first call on each device, with that device
-// current, looks the address up once with cudaGetSymbolAddress and caches
-// it.  That first call should come before any stream capture starts.
-// Every call shares the array and it keeps the last call's contents: each
-// call clears the part that must start at zero, and calls whose work
-// overlaps on the GPU race on it.
+// current, looks the address up with cudaGetSymbolAddress and caches it
+// together with the identity of the CUDA context it belongs to.  A later
+// call in another context of that device (the primary context released and
+// created again, or cudaDeviceReset) finds the identity changed and looks
+// the address up again, so a stale address is never handed to a kernel.
+// The call that does a look-up should come before any stream capture
+// starts: the first call on a device, and the first after its context was
+// replaced.  Every call shares the array and it keeps the last call's
+// contents: each call clears the part that must start at zero, and calls
+// whose work overlaps on the GPU race on it.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -46,7 +51,44 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char *g_scratch_ptr[kMaxDevices] = {};
+struct ScratchCache {
+    unsigned char *ptr;       // device address of g_noalloc_scratch
+    unsigned long long ctx;   // identity (cuCtxGetId) of the context it was looked up in
+};
+ScratchCache g_scratch[kMaxDevices] = {};
+
+// Driver entry points, resolved through the runtime (the library does not
+// link the driver library itself).
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_driver_resolved = false;
+
+bool resolve_driver_entry_points() {
+    if (g_driver_resolved) return g_ctx_get_current != nullptr && g_ctx_get_id != nullptr;
+    g_driver_resolved = true;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    return true;
+}
+
+// Identity of the CUDA context current on this thread (0: none current).
+bool current_context_id(unsigned long long *id) {
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0) return false;
+    *id = 0;
+    if (ctx == nullptr) return true;
+    return g_ctx_get_id(ctx, id) == 0;
+}
 
 sdeb_status fail(sdeb_status s, const char *fmt, long long a = 0, long long b = 0) {
     char buf[256];
@@ -55,23 +97,35 @@ sdeb_status fail(sdeb_status s, const char *fmt, long long a = 0, long long b = 
     return s;
 }
 
-// Device address of the scratch array on the current device.
+// Device address of the scratch array in the current device's current
+// context: the cached one while the context is the one it was looked up in,
+// else a fresh look-up.
 sdeb_status scratch_address(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(SDEB_ECUDA, "cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices) return fail(SDEB_EUNSUPPORTED, "device index %lld out of range", dev);
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_scratch_ptr[dev] == nullptr) {
+    if (!resolve_driver_entry_points()) return fail(SDEB_ECUDA, "driver context queries unavailable");
+    unsigned long long ctx = 0;
+    if (!current_context_id(&ctx)) return fail(SDEB_ECUDA, "cannot identify the current CUDA context");
+    if (ctx == 0 || g_scratch[dev].ptr == nullptr || g_scratch[dev].ctx != ctx) {
+        // The runtime makes the device's primary context current here when
+        // none was (a fresh thread or process).
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
+            g_scratch[dev] = ScratchCache{};
             return fail(SDEB_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
         }
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+        if (!current_context_id(&ctx) || ctx == 0) {
+            g_scratch[dev] = ScratchCache{};
+            return fail(SDEB_ECUDA, "no CUDA context current after the scratch look-up");
+        }
+        g_scratch[dev] = ScratchCache{static_cast<unsigned char *>(p), ctx};
     }
-    *out = g_scratch_ptr[dev];
+    *out = g_scratch[dev].ptr;
     return SDEB_OK;
 }
 

@@ -86,8 +86,10 @@ cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 // Host-side fault injection for failure-detection tests, nothing on the
 // device: SDEB_FAULT="alloc:<k>" makes the k-th allocation of a context's
 // buffers in this process (counted from 0) fail as out of memory,
-// "launch:<k>" makes the k-th forward launch fail without launching.  Read
-// once, at the first allocation or launch; any other value injects nothing.
+// "launch:<k>" makes the k-th forward launch of an integrate call
+// (sdeb_integrate, sdeb_integrate_range) fail without launching; the layout
+// tuner's trial launches are not counted.  Read once, at the first
+// allocation or launch; any other value injects nothing.
 struct FaultPlan {
     long alloc_at = -1, launch_at = -1;
     std::atomic<long> allocs{0}, launches{0};
@@ -1003,7 +1005,8 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
             e = cudaMemcpyAsync(tx, ctx->d_x, state_bytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess && tc) e = cudaMemsetAsync(tc, 0, (size_t)ctx->pb.orbits * ctx->pb.n * 4, s);
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess) e = launch_forward(a, l, ctx->pb.precision == SDEB_FP64, s);
+            // trial launches are not counted by the fault injection (SDEB_FAULT)
+            if (e == cudaSuccess) e = launch_forward_any(a, l, ctx->pb.precision == SDEB_FP64, s);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);

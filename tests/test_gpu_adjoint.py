@@ -14,6 +14,11 @@
   near the synchronisation transition, where the FP32 and FP64 trajectories
   themselves part), so there the check is per orbit: the median orbit agrees
   to 1e-4 and fewer than 5 % of orbits differ by more than 1e-3.
+* Per orbit on the adjoint workload at T = 5, against central finite
+  differences of the FP64 forward (common random numbers): the FP64 adjoint
+  of every orbit within 1e-6, the FP32 adjoint within 1e-3 except on
+  orbits whose gradient one FP32 ulp of x0 already moves by more than
+  2e-4 (at most 0.1 % of them; measured: 5 of 16384).
 """
 import ctypes
 
@@ -143,6 +148,74 @@ def test_adjoint_workload_fp32_vs_fp64():
     rel = np.abs(G32 - G64).max(axis=1) / np.abs(G64).max(axis=1)
     assert np.median(rel) < 1e-4, np.median(rel)
     assert (rel > 1e-3).mean() < 0.05, (rel > 1e-3).mean()
+
+
+def _per_orbit_r(precision, p, x0, W, steps):
+    """r_o(T) of every orbit (FP64 host array) for per-orbit parameters p."""
+    import torch
+    from paper_1908_03869_gb300.autograd import order_parameter
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    dt_t = torch.float64 if precision == "fp64" else torch.float32
+    n, orbits = x0.shape[1], x0.shape[0]
+    pb = sdeb.Problem.make("kuramoto", n, orbits, W["dt"], steps, 1, W["seed"], precision, no_frames=True)
+    with Integrator(pb) as it:
+        it.set_params(torch.tensor(p, dtype=dt_t).cuda(), torch.tensor(x0, dtype=dt_t).cuda())
+        it.integrate()
+        r = order_parameter(it.final())
+        return r.cpu().numpy().astype(np.float64)
+
+
+def test_adjoint_workload_fp32_per_orbit_vs_central_fd():
+    """Per-orbit pathwise gradients on the adjoint workload at T = 5 (500
+    steps) for K, sigma and three omegas, against central finite differences
+    of the FP64 forward with common random numbers (h = 1e-5, 1e-6, 1e-7
+    times max(|p_q|, 1), the best of them):
+      * the FP64 adjoint of every orbit within 1e-6 (relative to the orbit's
+        largest checked component);
+      * the FP32 adjoint of every orbit within 1e-3, except orbits whose
+        gradient the dynamics make sensitive to FP32 rounding: where one
+        FP32 ulp of x0 moves the FP64 gradient by more than 2e-4, the FP32
+        gradient (which carries a rounding every step) may differ by up to
+        30 times that move (about the square root of the step count); at
+        most 0.1 % of the orbits."""
+    W = inputs.WORKLOADS["kuramoto_adjoint_n32"]
+    orbits, steps, n = W["orbits"], 500, 32
+    p, x0 = inputs.kuramoto(n, orbits, seed=1, shared=True)
+    p, x0 = p.astype(np.float32).astype(np.float64), x0.astype(np.float32).astype(np.float64)
+    pt = np.tile(p, (orbits, 1))
+    qs = [0, 1, 2, 7, 33]                 # K, sigma and three omegas
+    G = {}
+    for prec in ("fp32", "fp64"):
+        _, g = _loss_and_grads(prec, pt, x0, W, steps, shared=False)
+        G[prec] = g[:, qs] * orbits       # d r_o / d p_o: the loss is the orbit mean
+    sign = np.where(np.sin(np.arange(n) * 7.1) >= 0, 1.0, -1.0)
+    _, g = _loss_and_grads("fp64", pt, x0 * (1 + 2.0 ** -24 * sign), W, steps, shared=False)
+    G["fp64_ulp"] = g[:, qs] * orbits
+
+    def rel(a, b):
+        return np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), 1e-300)
+
+    rel64, rel32 = np.full(orbits, np.inf), np.full(orbits, np.inf)
+    for rel_h in (1e-5, 1e-6, 1e-7):
+        fd = np.empty((orbits, len(qs)))
+        for j, q in enumerate(qs):
+            h = rel_h * max(abs(p[q]), 1.0)
+            pp, pm = pt.copy(), pt.copy()
+            pp[:, q] += h
+            pm[:, q] -= h
+            fd[:, j] = (_per_orbit_r("fp64", pp, x0, W, steps) - _per_orbit_r("fp64", pm, x0, W, steps)) / (2 * h)
+        rel64 = np.minimum(rel64, rel(G["fp64"], fd))
+        rel32 = np.minimum(rel32, rel(G["fp32"], fd))
+    sens = rel(G["fp64_ulp"], G["fp64"])
+    beyond = np.flatnonzero(rel32 >= 1e-3)
+    print("adjoint vs fd per orbit: fp64 max %.1e; fp32 median %.1e, max %.1e, %d orbits beyond 1e-3 "
+          "(one-ulp gradient sensitivity of those: %s)" % (rel64.max(), np.median(rel32), rel32.max(), beyond.size,
+                                                          ["%.1e" % v for v in sens[beyond]]))
+    assert rel64.max() < 1e-6, (int(np.argmax(rel64)), rel64.max())
+    assert beyond.size <= orbits // 1000
+    for o in beyond:
+        assert sens[o] > 2e-4 and rel32[o] < 30 * sens[o], (int(o), rel32[o], sens[o])
 
 
 def test_adjoint_workload_sampled_orbits_vs_oracle():

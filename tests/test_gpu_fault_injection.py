@@ -39,6 +39,24 @@ CHILD = textwrap.dedent("""
             it.set_params(pt, xt)
             it.integrate()
             print("RECOVERED", float(it.final().abs().sum()))
+    elif mode == "launch_tuned":
+        with Integrator(pb) as it:
+            it.set_params(pt, xt)
+            it.autotune(trial_steps=16)          # trial launches are not counted
+            it.integrate_range(0, 100)           # launch 0
+            try:
+                it.integrate_range(100, 200)     # launch 1: injected failure
+                print("UNEXPECTED launch succeeded")
+            except sdeb.SdebError as e:
+                print("STATUS", e.status, sdeb.sdeb_last_error(it.ctx))
+            it.integrate_range(100, 200)         # the counter stayed at 100
+            got = it.final().cpu().numpy()
+            lay = it.layout()
+        with Integrator(pb) as ref:
+            ref.set_layout(*lay)
+            ref.set_params(pt, xt)
+            ref.integrate()                      # launch 3
+            print("SAME", bool(np.array_equal(got, ref.final().cpu().numpy())))
     else:
         with Integrator(pb) as ref:
             ref.set_params(pt, xt)
@@ -83,4 +101,13 @@ def test_injected_launch_failure_is_ecuda_and_the_range_can_be_rerun():
     status_line = [l for l in out.splitlines() if l.startswith("STATUS")][0]
     assert int(status_line.split()[1]) == sdeb.SDEB_ECUDA
     assert "forward kernel launch" in status_line
+    assert "SAME True" in out
+
+
+def test_injected_launch_counts_integrate_calls_not_tuner_trials():
+    import paper_1908_03869_gb300 as sdeb
+    out = _child("launch_tuned", "launch:1")
+    assert "UNEXPECTED" not in out, out
+    status_line = [l for l in out.splitlines() if l.startswith("STATUS")][0]
+    assert int(status_line.split()[1]) == sdeb.SDEB_ECUDA
     assert "SAME True" in out

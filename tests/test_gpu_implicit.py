@@ -11,12 +11,16 @@ agree to rounding whether or not Newton has converged.
   over 200 steps of dt = 0.01 (frames and final state); the FP32 horizon is
   the one the Runge-Kutta path uses.  The n = 128 Kuramoto orbits without
   noise are chaotic: the FP64 oracle itself, with x0 perturbed by one
-  rounding (2.2e-16 relative), departs by 4.2e-13 at t = 3 and 1.9e-11 at
-  t = 4 under implicit Euler, so their FP64 horizon is 300 steps.
+  rounding (2^-52 relative), stays below 1e-12 through t = 3 and departs by
+  3.8e-12 (midpoint) and 2.9e-11 (Euler) by t = 4, so their FP64 horizon is
+  300 steps (pinned in test_oracle_sensitivity.py).
 * Large steps (dt = 0.2, K dt up to 0.8 for the Kuramoto orbits): FP64
-  <= 1e-12 over 30 steps, where Newton's later iterates matter.  The
-  near-critical orbits are sensitive: the oracle itself, with x0 perturbed
-  by one rounding, departs by up to 4e-13 at t = 6 and 2.5e-12 at t = 10.
+  <= 1e-12 over a horizon per case, where Newton's later iterates matter:
+  30 steps (t = 6) where the oracle itself, with x0 perturbed by one
+  rounding, departs past 1e-12 by t = 12 (Kuramoto n = 32 under Euler,
+  n = 100 under both schemes), 60 steps where that departure stays below
+  1e-13 (Kuramoto n = 32 under the midpoint rule, the FitzHugh-Nagumo
+  network); pinned in test_oracle_sensitivity.py (LARGE_STEP_HORIZON).
 * Every lane layout that covers an n = 32 orbit gives the oracle's orbit.
 * A stiff linear ODE (rate dt = 5): the closed forms (1 + h rate)^-k and
   ((1 - h rate / 2) / (1 + h rate / 2))^k, where Euler-Maruyama diverges.
@@ -31,6 +35,7 @@ from paper_1908_03869_gb300 import build as sdeb_build
 from paper_1908_03869_gb300 import inputs
 
 from helpers import max_rel_err, np_dtype, run_gpu, run_oracle
+from test_oracle_sensitivity import LARGE_STEP_HORIZON
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-12, "fp32": 1e-4}
@@ -92,8 +97,9 @@ def test_implicit_large_steps_match_oracle(scheme, model, n):
     p, x0 = _inputs(model, n, orbits)
     if model == "kuramoto":
         p[:, 0] = np.linspace(0.0, 4.0, orbits)     # K dt up to 0.8
-    fr, fin = _implicit(scheme, model, n, p, x0, "fp64", dt=0.2, steps=30, stride=10)
-    rfr, rfin = run_oracle(model, n, p, x0, 0.2, 30, 10, seed=2, orbit_offset=3, implicit=scheme)
+    steps = LARGE_STEP_HORIZON[(model, n, scheme)]
+    fr, fin = _implicit(scheme, model, n, p, x0, "fp64", dt=0.2, steps=steps, stride=10)
+    rfr, rfin = run_oracle(model, n, p, x0, 0.2, steps, 10, seed=2, orbit_offset=3, implicit=scheme)
     assert max_rel_err(fr, rfr) < 1e-12
     assert max_rel_err(fin, rfin) < 1e-12
 

@@ -5,8 +5,9 @@ integrators, Sec. 1.5) against the oracle's pinned RK4 step.
 * Every model: FP64 <= 1e-12 over 400 steps and FP32 <= 1e-4 over 200 steps
   of dt = 0.01 (frames and final state).  Without noise the n = 128
   Kuramoto orbits are chaotic enough that the FP64 oracle itself, with x0
-  perturbed by 6e-8 relative (one FP32 rounding), departs by 2.5e-6 at t = 1.5
-  and 4.6e-4 at t = 3.5: the FP32 horizon is t <= 2.
+  perturbed by 2^-24 relative (one FP32 rounding), departs by 2.6e-6 at
+  t = 1.5, 6.4e-6 at t = 2 and 1.7e-4 at t = 3: the FP32 horizon is t <= 2
+  (pinned in test_oracle_sensitivity.py).
 * No noise: Kuramoto with sigma > 0 gives the bits of sigma = 0.
 * Resume over step ranges is bit-exact.
 * Errors: a tuner-only layout (EUNSUPPORTED at integration), RK4 with

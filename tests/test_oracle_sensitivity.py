@@ -4,6 +4,7 @@ while synchronised orbits damp it.  This is why the GPU parity tests state a
 pathwise horizon (t <= 10) and bound the error beyond it by the dynamics'
 own sensitivity.  CPU only: oracle against oracle."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_1908_03869_gb300 import inputs
@@ -52,3 +53,91 @@ def test_fhn_network_amplifies_one_ulp():
     d = (np.abs(frp - fr) / np.maximum(np.abs(fr), 1.0)).max(axis=(1, 2))
     assert d[0] < 1e-7
     assert d.max() > 20 * 2.0 ** -24
+
+
+# ---------------------------------------------------------------------------
+# The ODE-path parity horizons.  Each GPU test of the Runge-Kutta and implicit
+# schemes states a horizon; these pins show, on the oracle alone, how far a
+# one-rounding perturbation of the initial state carries on the same inputs
+# (the GPU tests' seeds and orbit offsets), so each horizon ends where the
+# dynamics, not the kernel, would push an implementation that differs from
+# the oracle by roundings past the tolerance.
+# ---------------------------------------------------------------------------
+
+def _ode_divergence(model, n, p, x0, dt, steps, stride, rel, orbit_begin=3, **kw):
+    """max over state components of |x' - x| / max(|x|, 1), per frame and
+    orbit, x' integrated from x0 (1 + rel s) with a fixed sign pattern s."""
+    import concurrent.futures
+    m, d = {"kuramoto": (n, n + 2), "fhn_net": (n // 2, 6)}[model]
+    pb = oracle.make_problem(model, n, m, d, dt, steps, stride, 2, **kw)
+    sign = np.where(np.sin(np.arange(n) * 7.1) >= 0, 1.0, -1.0)
+    with concurrent.futures.ThreadPoolExecutor(2) as ex:   # the oracle releases the GIL
+        runs = list(ex.map(lambda x: oracle.integrate(pb, p, x, orbit_begin=orbit_begin, nthreads=2)[0],
+                           [x0, x0 * (1 + rel * sign)]))
+    return (np.abs(runs[1] - runs[0]) / np.maximum(np.abs(runs[0]), 1.0)).max(axis=2)
+
+
+def test_rk4_noiseless_n128_fp32_horizon():
+    # tests/test_gpu_rk4.py, Kuramoto n = 128 (inputs seed 31, FP32-rounded),
+    # dt = 0.01, no noise: one FP32 rounding (2^-24) of x0 stays below the
+    # 1e-4 tolerance through t = 2 (the FP32 horizon, 200 steps) and passes
+    # it by t = 3.5.  Orbit 171 is the most sensitive of the test's 200.
+    p, x0 = inputs.kuramoto(128, 200, seed=31)
+    sub = [171, 25]
+    p = p[sub].astype(np.float32).astype(np.float64)
+    x0 = x0[sub].astype(np.float32).astype(np.float64)
+    d = _ode_divergence("kuramoto", 128, p, x0, 0.01, 350, 50, 2.0 ** -24, rk4=True).max(axis=1)
+    # frames every 0.5: t = 0, 0.5, ..., 3.5
+    assert d[:5].max() < 1e-5          # t <= 2: 6.4e-6
+    assert d[3] > 1e-6                 # t = 1.5: 2.6e-6, growing
+    assert d[6:].max() > 1e-4          # t = 3 .. 3.5: 1.7e-4 .. 3.2e-4
+
+
+@pytest.mark.parametrize("scheme,orbit", [("euler", 15), ("midpoint", 33)])
+def test_implicit_noiseless_n128_fp64_horizon(scheme, orbit):
+    # tests/test_gpu_implicit.py, Kuramoto n = 128 (inputs seed 41), dt =
+    # 0.01, 4 Newton iterations a step: one FP64 rounding (2^-52) of x0 stays
+    # below the 1e-12 tolerance through t = 3 (the FP64 horizon, 300 steps)
+    # and passes it by t = 4 (orbit 15 under implicit Euler, 33 under the
+    # midpoint rule: the most sensitive of the test's 200 orbits).
+    p, x0 = inputs.kuramoto(128, 200, seed=41)
+    d = _ode_divergence("kuramoto", 128, p[[orbit]], x0[[orbit]], 0.01, 400, 50, 2.0 ** -52,
+                        orbit_begin=3 + orbit, implicit=scheme)[:, 0]
+    # frames every 0.5: t = 0 .. 4
+    assert d[:7].max() < 1e-12         # t <= 3
+    assert d[7:].max() > 3e-12         # t = 3.5 .. 4: 3.8e-12 .. 2.9e-11
+
+
+@pytest.mark.parametrize("scheme", ["euler", "midpoint"])
+@pytest.mark.parametrize("model,n", [("kuramoto", 32), ("kuramoto", 100), ("fhn_net", 64)])
+def test_implicit_large_step_fp64_horizons(scheme, model, n):
+    # tests/test_gpu_implicit.py, dt = 0.2 (K dt up to 0.8 for the Kuramoto
+    # orbits), 128 orbits: where one FP64 rounding of x0 carries past 1e-12
+    # within t = 12 the GPU test's horizon is 30 steps (t = 6); where it
+    # stays below 1e-13 through t = 12 the horizon is 60 steps.
+    orbits = 128
+    if model == "kuramoto":
+        p, x0 = inputs.kuramoto(n, orbits, seed=41)
+        p[:, 0] = np.linspace(0.0, 4.0, orbits)
+        kw = dict(mean_field=n > 64)
+    else:
+        p, x0 = inputs.fhn(n // 2, orbits, seed=43)
+        kw = {}
+    d = _ode_divergence(model, n, p, x0, 0.2, 60, 5, 2.0 ** -52, implicit=scheme, **kw).max(axis=1)
+    # frames every t = 1, t = 0 .. 12
+    if LARGE_STEP_HORIZON[(model, n, scheme)] == 30:
+        assert d.max() > 1e-12
+    else:
+        assert d.max() < 1e-13
+
+
+# Horizons (steps of dt = 0.2) of the large-step FP64 parity test of the
+# implicit schemes, as the pins above support them.
+LARGE_STEP_HORIZON = {
+    ("kuramoto", 32, "euler"): 30,       # 1.7e-12 at t = 10
+    ("kuramoto", 32, "midpoint"): 60,    # below 1e-13 through t = 12
+    ("kuramoto", 100, "euler"): 30,      # 2.0e-12 at t = 8
+    ("kuramoto", 100, "midpoint"): 30,   # 1.0e-12 at t = 4
+    ("fhn_net", 64, "euler"): 60,        # below 1e-13 through t = 12
+    ("fhn_net", 64, "midpoint"): 60,
+}
