@@ -312,6 +312,34 @@ SDEB_API sdeb_status sdeb_read_orbits(sdeb_ctx *ctx, void *dst, size_t dst_bytes
 SDEB_API sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t dst_on_device,
                             void *stream);
 
+/* Ensemble moments of the stored frames, accumulated in FP64 on the GPU
+ * whatever the context precision.  The paper's accuracy experiment reports
+ * the mean and the standard deviation over realisations of the order
+ * parameter r(t) of Eq. 7 (Sec. 2.3); with many orbits the statistics are
+ * formed where the frames are, and only these moments leave the device.
+ * For the frames [frame_begin, frame_begin + frame_count):
+ *   mom  [frame_count][n][2] (or NULL): per frame and state component, the
+ *        mean over orbits and the population variance (divisor = orbits);
+ *   rmom [frame_count][2] (or NULL): per frame, the mean over orbits and
+ *        the population variance of r = |(1/n) sum_j exp(i x_j)| (Eq. 7);
+ *        phase models only (SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER), else
+ *        EUNSUPPORTED.  r of an orbit is formed in the context precision
+ *        (FP32: sine and cosine of the phase reduced to [-pi, pi] from the
+ *        special-function unit), then accumulated in FP64.
+ * The sums run in a fixed order -- chunks of 4096 orbits, shifted sums per
+ * thread, combined by Chan, Golub and LeVeque's pairwise update in thread
+ * and chunk order -- so every call gives the same bits for a frame, whatever
+ * frame range it asks for.  mom_bytes / rmom_bytes must equal the sizes
+ * above (ignored for a NULL pointer; at least one pointer non-NULL).
+ * ESTATE for a context without frames, before sdeb_set_params, or for frames
+ * past the current step; EINVAL for a range outside [0, F).  dst_on_device:
+ * SDEB_MEM_* for both outputs.  Allocates its scratch stream-ordered
+ * (cudaMallocAsync) and frees it on the stream.  Not for batches
+ * (EUNSUPPORTED). */
+SDEB_API sdeb_status sdeb_frame_moments(sdeb_ctx *ctx, int64_t frame_begin, int64_t frame_count, double *mom,
+                                        size_t mom_bytes, double *rmom, size_t rmom_bytes, int32_t dst_on_device,
+                                        void *stream);
+
 /* Pathwise gradient by the discrete adjoint of Eq. 2 (checkpointed
  * recompute, Philox noise regenerated).  Requires ckpt_every > 0 and a
  * completed integration to k = steps.  All pointers are device pointers of

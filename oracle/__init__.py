@@ -201,3 +201,22 @@ def order_param(theta):
     dr = np.zeros(th.shape[-1])
     lib().oracle_order_param(th.shape[-1], _ptr(th), _ptr(r), _ptr(dr))
     return float(r[0]), dr
+
+
+def frame_moments(frames, order_parameter=False):
+    """Ensemble moments of frames [F][orbits][n] over the orbits, FP64, by
+    definition (two passes): mom [F][n][2] = (mean, population variance
+    mean((x - mean)^2)) of every state component; with order_parameter, also
+    rmom [F][2] = (mean, population variance) of r = |(1/n) sum_j
+    exp(i x_j)|, the order parameter of Eq. 7 (Sec. 2.3: the statistics of
+    r over realisations that the paper's accuracy experiment reports)."""
+    fr = np.asarray(frames, dtype=np.float64)
+    mean = fr.mean(axis=1)
+    var = ((fr - mean[:, None, :]) ** 2).mean(axis=1)
+    mom = np.stack([mean, var], axis=-1)
+    if not order_parameter:
+        return mom, None
+    r = np.abs(np.exp(1j * fr).mean(axis=2))            # [F][orbits]
+    rmean = r.mean(axis=1)
+    rvar = ((r - rmean[:, None]) ** 2).mean(axis=1)
+    return mom, np.stack([rmean, rvar], axis=-1)

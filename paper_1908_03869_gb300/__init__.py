@@ -23,7 +23,7 @@ __all__ = [
     "SDEB_FP32_KAHAN", "SDEB_FP64", "SDEB_FLAG_SHARED_PARAMS", "SDEB_FLAG_NO_FRAMES", "SDEB_FLAG_MILSTEIN",
     "SDEB_FLAG_RK4", "SDEB_FLAG_IMPLICIT_EULER", "SDEB_FLAG_IMPLICIT_MIDPOINT",
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
-    "sdeb_read_orbits", "sdeb_read_final", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
+    "sdeb_read_orbits", "sdeb_read_final", "sdeb_frame_moments", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
     "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
     "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "sdeb_batch_plan", "model_shape",
@@ -106,6 +106,8 @@ _SIGS = {
     "sdeb_integrate_range": (_ST, [_P, ctypes.c_int64, ctypes.c_int64, _P]),
     "sdeb_read_orbits": (_ST, [_P, _P, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P]),
     "sdeb_read_final": (_ST, [_P, _P, ctypes.c_size_t, ctypes.c_int32, _P]),
+    "sdeb_frame_moments": (_ST, [_P, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_size_t, _P, ctypes.c_size_t,
+                                 ctypes.c_int32, _P]),
     "sdeb_grad": (_ST, [_P, _P, _P, _P, _P]),
     "sdeb_orbit_flags": (_ST, [_P, _P, _P]),
     "sdeb_frames_device_ptr": (_ST, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),
@@ -203,6 +205,11 @@ def sdeb_read_orbits(ctx, dst, dst_bytes, frame_begin, frame_count, dst_on_devic
 
 def sdeb_read_final(ctx, dst, dst_bytes, dst_on_device, stream=None):
     _check(lib().sdeb_read_final(ctx, dst, dst_bytes, int(dst_on_device), _stream(stream)), ctx)
+
+
+def sdeb_frame_moments(ctx, frame_begin, frame_count, mom, mom_bytes, rmom, rmom_bytes, dst_on_device, stream=None):
+    _check(lib().sdeb_frame_moments(ctx, frame_begin, frame_count, mom, mom_bytes, rmom, rmom_bytes,
+                                    int(dst_on_device), _stream(stream)), ctx)
 
 
 def sdeb_grad(ctx, dL_dxK, dL_dp, dL_dx0=None, stream=None):

@@ -183,6 +183,27 @@ inline bool default_layout(int units, Layout &l) {
     return true;
 }
 
+// ---- Ensemble moments of stored frames (moments.cu) ------------------------
+// Orbits per chunk of the FP64 moment accumulation: fixed, so a frame's bits
+// do not depend on the frame range of a call.
+constexpr int64_t kMomChunk = 4096;
+
+struct FrameMomentsPlan {
+    int chunks = 1;               // ceil(orbits / kMomChunk)
+    int64_t frames_per_pass = 1;  // frames whose partials fit the scratch at once
+    size_t partial_bytes = 0;     // scratch for one pass's partials
+    size_t out_bytes = 0;         // one pass's results ([frames][n][2] + [frames][2] doubles)
+};
+FrameMomentsPlan frame_moments_plan(int64_t orbits, int n, int64_t count);
+// Moments of frames [f0, f0 + count) (count <= plan.frames_per_pass) of a
+// [F][orbits][n] frame buffer: state_out [count][n][2] = (mean, variance) of
+// every component over the orbits, r_out [count][2] = (mean, variance) of
+// the order parameter of Eq. 7; either may be nullptr.  partial: device
+// scratch of plan.partial_bytes.
+cudaError_t launch_frame_moments_pass(const void *frames, bool fp64, int64_t orbits, int n, int64_t f0,
+                                      int64_t count, const FrameMomentsPlan &plan, void *partial,
+                                      double *state_out, double *r_out, cudaStream_t s);
+
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_philox_fill(uint64_t seed, uint32_t k0, int64_t nk, uint32_t b0, int64_t nb,
                                uint32_t o0, int64_t no, uint32_t stream_id, uint32_t *out,

@@ -912,6 +912,63 @@ sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t 
     return SDEB_OK;
 }
 
+sdeb_status sdeb_frame_moments(sdeb_ctx *ctx, int64_t frame_begin, int64_t frame_count, double *mom,
+                               size_t mom_bytes, double *rmom, size_t rmom_bytes, int32_t dst_on_device,
+                               void *stream) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "moments are per context, not per batch");
+    if (!mom && !rmom) return fail(ctx, SDEB_EINVAL, "mom and rmom are both NULL");
+    if (!mem_kind_valid(dst_on_device)) return fail(ctx, SDEB_EINVAL, "dst_on_device %d is not SDEB_MEM_*", dst_on_device);
+    const bool phase = ctx->pb.model == SDEB_KURAMOTO || ctx->pb.model == SDEB_KURAMOTO_PAPER;
+    if (rmom && !phase) return fail(ctx, SDEB_EUNSUPPORTED, "the order parameter needs a phase model");
+    if (!ctx->d_frames) return fail(ctx, SDEB_ESTATE, "context was created without frames");
+    if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
+    if (frame_begin < 0 || frame_count < 0 || frame_begin + frame_count > ctx->nframes)
+        return fail(ctx, SDEB_EINVAL, "frames [%lld, %lld) outside [0, %lld)", (long long)frame_begin,
+                    (long long)(frame_begin + frame_count), (long long)ctx->nframes);
+    if (frame_count > 0 && (frame_begin + frame_count - 1) * ctx->pb.stride > ctx->k_current)
+        return fail(ctx, SDEB_ESTATE, "frame %lld is past the current step %lld",
+                    (long long)(frame_begin + frame_count - 1), (long long)ctx->k_current);
+    const int n = ctx->pb.n;
+    if (mom && mom_bytes != (size_t)frame_count * n * 2 * sizeof(double))
+        return fail(ctx, SDEB_EINVAL, "mom_bytes=%zu, expected %zu", mom_bytes,
+                    (size_t)frame_count * n * 2 * sizeof(double));
+    if (rmom && rmom_bytes != (size_t)frame_count * 2 * sizeof(double))
+        return fail(ctx, SDEB_EINVAL, "rmom_bytes=%zu, expected %zu", rmom_bytes,
+                    (size_t)frame_count * 2 * sizeof(double));
+    if (frame_count == 0) return SDEB_OK;
+    const cudaStream_t s = as_stream(stream);
+    const bool fp64 = ctx->pb.precision == SDEB_FP64;
+    const bool to_host = dst_on_device != SDEB_MEM_DEVICE;
+    const FrameMomentsPlan plan = frame_moments_plan(ctx->pb.orbits, n, frame_count);
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, plan.partial_bytes + (to_host ? plan.out_bytes : 0), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sdeb_frame_moments scratch");
+    }
+    double *stage = to_host ? reinterpret_cast<double *>(static_cast<char *>(scratch) + plan.partial_bytes) : nullptr;
+    for (int64_t f = 0; f < frame_count && e == cudaSuccess; f += plan.frames_per_pass) {
+        const int64_t cnt = std::min<int64_t>(plan.frames_per_pass, frame_count - f);
+        double *st = mom ? (to_host ? stage : mom + f * n * 2) : nullptr;
+        double *rt = rmom ? (to_host ? stage + cnt * n * 2 : rmom + f * 2) : nullptr;
+        e = launch_frame_moments_pass(ctx->d_frames, fp64, ctx->pb.orbits, n, frame_begin + f, cnt, plan, scratch,
+                                      st, rt, s);
+        if (e == cudaSuccess && to_host && mom)
+            e = cudaMemcpyAsync(mom + f * n * 2, st, (size_t)cnt * n * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && to_host && rmom)
+            e = cudaMemcpyAsync(rmom + f * 2, rt, (size_t)cnt * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess && dst_on_device == SDEB_MEM_HOST) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sdeb_frame_moments");
+    }
+    return SDEB_OK;
+}
+
 sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream) {
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (!dst) return fail(ctx, SDEB_EINVAL, "dst is NULL");

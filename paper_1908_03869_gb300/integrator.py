@@ -10,7 +10,7 @@ import torch
 
 from . import (SDEB_FLAG_NO_FRAMES, SDEB_FLAG_SHARED_PARAMS, SDEB_FP64, SDEB_MEM_DEVICE, SDEB_MEM_HOST,
                SDEB_MEM_HOST_ASYNC, Problem, sdeb_autotune, sdeb_create,
-               sdeb_destroy, sdeb_get_layout, sdeb_grad, sdeb_integrate, sdeb_integrate_range, sdeb_orbit_flags,
+               sdeb_destroy, sdeb_frame_moments, sdeb_get_layout, sdeb_grad, sdeb_integrate, sdeb_integrate_range, sdeb_orbit_flags,
                sdeb_read_final, sdeb_read_orbits, sdeb_set_layout, sdeb_set_params)
 
 
@@ -117,6 +117,20 @@ class Integrator:
         sdeb_read_final(self.ctx, _ptr(out), out.numel() * out.element_size(), _mem(out, async_host),
                         self._stream(stream))
         return out
+
+    def moments(self, begin=0, count=None, state=True, order_param=False, device="cuda", stream=None):
+        """FP64 ensemble moments of frames [begin, begin + count) over the
+        orbits (sdeb_frame_moments): (mom [count][n][2] or None, rmom
+        [count][2] or None), each pair (mean, population variance); rmom is
+        that of the order parameter of Eq. 7 (phase models)."""
+        count = self.nframes - begin if count is None else count
+        mom = torch.empty((count, self.pb.n, 2), dtype=torch.float64, device=device) if state else None
+        rmom = torch.empty((count, 2), dtype=torch.float64, device=device) if order_param else None
+        kind = mom if mom is not None else rmom
+        sdeb_frame_moments(self.ctx, begin, count, _ptr(mom) if mom is not None else None,
+                           mom.numel() * 8 if mom is not None else 0, _ptr(rmom) if rmom is not None else None,
+                           rmom.numel() * 8 if rmom is not None else 0, _mem(kind, False), self._stream(stream))
+        return mom, rmom
 
     def flags(self, stream=None):
         out = torch.zeros(self.pb.orbits, dtype=torch.uint8)
