@@ -410,6 +410,18 @@ SDEB_API sdeb_status sdeb_normals_fill(uint64_t seed, uint32_t k0, int64_t nk, u
 SDEB_API sdeb_status sdeb_order_param(const void *theta, int64_t orbits, int32_t n, int32_t precision,
                              void *r, void *dr, void *stream);
 
+/* ---- Pipe rates of this GPU (the benchmark's roofline peaks) ------------
+ * No counterpart in the paper.  Measures the issue rate of one arithmetic
+ * pipe in results per SM per clock: pipe 0 = SFU sine (sin.approx.ftz.f32),
+ * 1 = SFU base-2 logarithm, 2 = SFU square root (sqrt.approx.ftz.f32),
+ * 3 = FP64 fused multiply-add, 4 = FP32 fused multiply-add.  One block of
+ * 1024 threads per SM runs 8 independent chains of `iters` (1 .. 2^24)
+ * dependent operations per thread; the median over the SMs of the block's
+ * clock64 cycles divides its 8192 * iters operations.  The rate per clock is
+ * independent of the clock frequency.  Synchronises `stream`; allocates
+ * stream-ordered scratch.  EINVAL on a bad argument, ECUDA on a failure. */
+SDEB_API sdeb_status sdeb_pipe_rate(int32_t pipe, int32_t iters, double *ops_per_clk_per_sm, void *stream);
+
 /* ---- Allocation-free forward integration ------------------------------
  * No counterpart in the paper.  For callers that cannot allocate device
  * memory -- code running while a CUDA graph is captured, hosts whose own

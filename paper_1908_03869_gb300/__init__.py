@@ -25,9 +25,9 @@ __all__ = [
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_frame_moments", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
-    "sdeb_integrate_noalloc", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
+    "sdeb_integrate_noalloc", "sdeb_pipe_rate", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
     "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "sdeb_batch_plan", "model_shape",
-    "sdeb_swarm_expand", "sdeb_swarm_fitness", "sdeb_swarm_update", "SDEB_SWARM_MAX_DIMS",
+    "sdeb_swarm_expand", "sdeb_swarm_fitness", "sdeb_swarm_update", "SDEB_SWARM_MAX_DIMS", "PIPES",
     "SDEB_MEM_HOST", "SDEB_MEM_DEVICE", "SDEB_MEM_HOST_ASYNC",
     "EXPORTED_SYMBOLS",
 ]
@@ -119,6 +119,7 @@ _SIGS = {
                                 ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "sdeb_order_param": (_ST, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "sdeb_integrate_noalloc": (_ST, [ctypes.POINTER(Problem), _P, _P, _P, _P, _P]),
+    "sdeb_pipe_rate": (_ST, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
     "sdeb_set_layout": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sdeb_get_layout": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sdeb_autotune": (_ST, [_P, ctypes.c_int64, _P]),
@@ -338,6 +339,16 @@ def sdeb_swarm_update(x, v, pbest, pbest_fit, fit, particles, lo, hi, w, c1, c2,
         raise ValueError("lo and hi need one bound per dimension")
     _check(lib().sdeb_swarm_update(x, v, pbest, pbest_fit, fit, particles, len(lo), lo_a, hi_a, float(w), float(c1),
                                    float(c2), seed & 0xFFFFFFFFFFFFFFFF, generation, gbest, _stream(stream)))
+
+
+PIPES = {"sfu_sin": 0, "sfu_lg2": 1, "sfu_sqrt": 2, "fp64_fma": 3, "fp32_fma": 4}
+
+
+def sdeb_pipe_rate(pipe, iters=1024, stream=None):
+    """Measured results per SM per clock of one pipe (a name of PIPES or its number)."""
+    out = ctypes.c_double()
+    _check(lib().sdeb_pipe_rate(PIPES.get(pipe, pipe), iters, ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def sdeb_integrate_noalloc(problem, params, x0, x_final, frames=None, stream=None):
