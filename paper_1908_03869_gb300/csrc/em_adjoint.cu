@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
     const Real *ckpt = static_cast<const Real *>(a.ckpt);
     Real *seg = static_cast<Real *>(a.seg);
     WarpGroupSum<G> reduce;
+    const NoiseLane<P> noise(gorb, u0, a.keys);
     const int64_t nseg = ((int64_t)a.steps + a.ckpt_every - 1) / a.ckpt_every;
 
     for (int64_t c = nseg - 1; c >= 0; --c) {
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             Real r[1][P], z[1][P];
 #pragma unroll
             for (int i = 0; i < P; ++i) r[0][i] = reduce_phase(x[0][i], cp[0][i]);
-            em_step<M, Real, P, true>(model, x, cp, k, gorb, u0, units, a.keys, reduce, &z[0]);
+            em_step<M, Real, P, true>(model, x, cp, k, noise, u0, units, a.keys, reduce, &z[0]);
             if (active) {
                 Real *row = seg + ((int64_t)(k - k0) * a.orbits + o) * (2 * n);
                 store_units<Real, 1, P>(row, units, u0, r);

@@ -54,6 +54,7 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
     Real *frames = a.frames != nullptr && in.has_frames ? static_cast<Real *>(a.frames) + in.f_off : nullptr;
     if (has && frames != nullptr) store_units<Real, 1, P>(frames + (int64_t)it.orbit * n, units, u0, x);
     const uint32_t gorb = in.orbit_offset + (uint32_t)it.orbit;
+    const NoiseLane<P> noise(gorb, u0, a.keys);
     const uint32_t steps = in.steps;
     uint32_t to_frame = in.stride;
     // Steps run in runs that end at the next event (a frame or the end) of
@@ -66,7 +67,7 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
         if (live) mine = min(mine, min(to_frame, steps - k));
         const uint32_t run = __reduce_min_sync(0xffffffffu, mine);
 #pragma unroll 1
-        for (uint32_t s = 0; s < run; ++s) em_step<M, Real, P>(model, x, cp, k + s, gorb, u0, units, a.keys, reduce);
+        for (uint32_t s = 0; s < run; ++s) em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
         k += run;
         if (live) {
             to_frame -= run;

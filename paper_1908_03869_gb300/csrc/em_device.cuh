@@ -64,6 +64,29 @@ __device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     return U32x4{c0, c1, c2, c3};
 }
 
+// Counters (c0, c1, c2, 0) whose words c1 and c2 stay fixed while c0 runs
+// (the noise counter (k, block, orbit, 0) of one lane): the first round's
+// product of c2 and its mix with c1 and the round key depend only on the fixed
+// words, so they are formed once (philox_round1_fixed), and each counter then
+// costs one product and one xor for round 1 (c3 = 0 drops out of the mix).
+struct PhiloxRound1 {
+    uint32_t n0;   // hi(M1 c2) ^ c1 ^ key0 of round 1: word 0 after round 1
+    uint32_t lo1;  // lo(M1 c2): word 1 after round 1
+};
+
+__device__ __forceinline__ PhiloxRound1 philox_round1_fixed(uint32_t c1, uint32_t c2, const PhiloxKeys &keys) {
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    return PhiloxRound1{(uint32_t)(p1 >> 32) ^ c1 ^ keys.k0[0], (uint32_t)p1};
+}
+
+__device__ __forceinline__ U32x4 philox4x32_10_fixed(uint32_t c0, const PhiloxRound1 &f, const PhiloxKeys &keys) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint32_t x0 = f.n0, x1 = f.lo1, x2 = (uint32_t)(p0 >> 32) ^ keys.k1[0], x3 = (uint32_t)p0;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) philox_round(x0, x1, x2, x3, keys.k0[r], keys.k1[r]);
+    return U32x4{x0, x1, x2, x3};
+}
+
 // Host-side key schedule: round r uses (k0 + r W0, k1 + r W1), W0/W1 the two
 // Weyl increments (32-bit fractions of the golden ratio and of sqrt(3) - 1).
 inline PhiloxKeys philox_key_schedule(uint64_t seed) {
@@ -134,46 +157,70 @@ __device__ __forceinline__ void sincos_approx_f32(float x, float &s, float &c) {
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
-// FP32.  y = -2 ln U1 comes from the SFU log2 except when U1 is within 2^-6
-// of 1, where the absolute error of an SFU logarithm would dominate: there
+// FP32, in polar form: the pair is (amp c, amp s), amp = -radius.
+// y = -2 ln U1 comes from the SFU log2 except when U1 is within 2^-6 of 1,
+// where the absolute error of an SFU logarithm would dominate: there
 // t = 1 - U1 = (~w + 1/2) 2^-32 comes from the complement word and
-// -2 ln(1 - t) = t (2 + t + 2t^2/3 + t^3/2 + 2t^4/5) + O(t^6), the dropped
-// terms below 2^-26 relative for t <= 2^-6.  The angle is 2 pi (U2 - 1/2)
-// from the centred word in one rounding, an argument in [-pi, pi] for the
-// SFU: cos(2 pi U2) = -cos(2 pi (U2 - 1/2)), likewise for sin.
-__device__ __forceinline__ void box_muller_f32(uint32_t w_first, uint32_t w_second, float &n_cos,
-                                               float &n_sin) {
+// -2 ln(1 - t) = t (2 + t + 2t^2/3 + t^3/2) + O(t^5), the dropped terms
+// (2t^5/5 + ...) below t^4/5 <= 2^-24/5 relative for t <= 2^-6.  The angle
+// is 2 pi (U2 - 1/2) from the centred word in one rounding, an argument in
+// [-pi, pi] for the SFU: cos(2 pi U2) = -cos(2 pi (U2 - 1/2)), likewise for
+// sin, hence the negative amplitude.
+__device__ __forceinline__ void box_muller_polar_f32(uint32_t w_first, uint32_t w_second, float &amp, float &c,
+                                                     float &s) {
     const float kMinus2Ln2 = -1.38629436111989061883f;  // -2 ln 2
     // For w >= 2^31 the signed reading of w is w - 2^32 = -(comp + 1), comp =
     // 2^32 - 1 - w the complement word, so t = 1 - U1 = (comp + 1/2) 2^-32 is
     // one fma of it; t is only used when comp < 2^26.
     const float t = __fmaf_rn(__int2float_rn((int32_t)w_first), -0x1p-32f, -0x1p-33f);
-    float poly = __fmaf_rn(t, 0.4f, 0.5f);
-    poly = __fmaf_rn(poly, t, 2.0f / 3.0f);
+    float poly = __fmaf_rn(t, 0.5f, 2.0f / 3.0f);
     poly = __fmaf_rn(poly, t, 1.0f);
     poly = __fmaf_rn(poly, t, 2.0f);
     const float y_series = t * poly;
     const float y_log = kMinus2Ln2 * lg2_approx_f32(uniform_f32(w_first));
     const float y = (w_first > 0xFBFFFFFFu) ? y_series : y_log;  // comp < 2^26
-    const float radius = sqrt_approx_f32(y);
+    amp = -sqrt_approx_f32(y);
     // float(2 pi) 2^-32 and float(2 pi) 2^-33: exact scalings of float(2 pi)
     const float ang = __fmaf_rn(__int2float_rn((int32_t)(w_second ^ 0x80000000u)), 0x1.921fb6p-30f,
                                 0x1.921fb6p-31f);
-    float s, c;
     sincos_approx_f32(ang, s, c);
-    n_cos = -radius * c;
-    n_sin = -radius * s;
+}
+
+__device__ __forceinline__ void box_muller_f32(uint32_t w_first, uint32_t w_second, float &n_cos,
+                                               float &n_sin) {
+    float amp, c, s;
+    box_muller_polar_f32(w_first, w_second, amp, c, s);
+    n_cos = amp * c;
+    n_sin = amp * s;
+}
+
+// FP64, polar form: amp = radius, (c, s) = (cos, sin)(2 pi U2).
+__device__ __forceinline__ void box_muller_polar_f64(uint32_t w_first, uint32_t w_second, double &amp,
+                                                     double &c, double &s) {
+    const double u1 = uniform_f64(w_first);
+    const double u2 = uniform_f64(w_second);
+    amp = sqrt(-2.0 * log(u1));
+    sincospi(2.0 * u2, &s, &c);
 }
 
 __device__ __forceinline__ void box_muller_f64(uint32_t w_first, uint32_t w_second, double &n_cos,
                                                double &n_sin) {
-    double u1 = uniform_f64(w_first);
-    double u2 = uniform_f64(w_second);
-    double radius = sqrt(-2.0 * log(u1));
-    double s, c;
-    sincospi(2.0 * u2, &s, &c);
-    n_cos = radius * c;
-    n_sin = radius * s;
+    double amp, c, s;
+    box_muller_polar_f64(w_first, w_second, amp, c, s);
+    n_cos = amp * c;
+    n_sin = amp * s;
+}
+
+template <typename Real>
+__device__ __forceinline__ void box_muller_polar(uint32_t w_first, uint32_t w_second, Real &amp, Real &c, Real &s);
+template <>
+__device__ __forceinline__ void box_muller_polar<float>(uint32_t a, uint32_t b, float &amp, float &c, float &s) {
+    box_muller_polar_f32(a, b, amp, c, s);
+}
+template <>
+__device__ __forceinline__ void box_muller_polar<double>(uint32_t a, uint32_t b, double &amp, double &c,
+                                                         double &s) {
+    box_muller_polar_f64(a, b, amp, c, s);
 }
 
 template <typename Real>

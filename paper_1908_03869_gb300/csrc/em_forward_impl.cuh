@@ -104,26 +104,46 @@ struct TeamSum {
     }
 };
 
-// The step's normals for the lane's P units: per noise block one Philox call
-// (counter (k, block, orbit, 0)) and Box-Muller.  A lane holding 1 or 2
-// units draws the block that contains them and transforms only the word pair
-// that holds them (several lanes of a group draw the same block).
-template <typename Real, int P>
-__device__ __forceinline__ void draw_normals(Real (&z)[P], uint32_t k, uint32_t orbit, int u0,
-                                             const PhiloxKeys &keys) {
-    if constexpr (P < 4) {
-        const U32x4 w = philox4x32_10(k, (uint32_t)(u0 >> 2), orbit, 0u, keys);
-        const bool high = (u0 & 2) != 0;
-        Real zz[2];
-        box_muller<Real>(high ? w.z : w.x, high ? w.w : w.y, zz[0], zz[1]);
+// The lane's fixed Philox words: round 1 of the noise counters (k, block,
+// orbit, 0) of its blocks without k, formed once per launch.
+template <int P>
+struct NoiseLane {
+    static constexpr int NB = P < 4 ? 1 : P / 4;
+    PhiloxRound1 r1[NB];
+    __device__ __forceinline__ NoiseLane(uint32_t orbit, int u0, const PhiloxKeys &keys) {
 #pragma unroll
-        for (int i = 0; i < P; ++i) z[i] = (P == 1 && (u0 & 1)) ? zz[1] : zz[i];
+        for (int blk = 0; blk < NB; ++blk) r1[blk] = philox_round1_fixed((uint32_t)(u0 >> 2) + blk, orbit, keys);
+    }
+};
+
+// Normal pairs of a step in polar form: the lane's P normals are
+// N_i = amp[pair(i)] * trig[i], pair(i) = i / 2 (one pair when P < 4).  Per
+// noise block one Philox call (counter (k, block, orbit, 0)) and two
+// Box-Muller pairs.  A lane holding 1 or 2 units draws the block that
+// contains them and transforms only the word pair that holds them (several
+// lanes of a group draw the same block).
+template <int P>
+constexpr int kNoisePairs = P < 4 ? 1 : P / 2;
+
+template <int P>
+__device__ __forceinline__ constexpr int noise_pair(int i) { return P < 4 ? 0 : i / 2; }
+
+template <typename Real, int P>
+__device__ __forceinline__ void draw_noise(Real (&amp)[kNoisePairs<P>], Real (&trig)[P], uint32_t k, int u0,
+                                           const NoiseLane<P> &nl, const PhiloxKeys &keys) {
+    if constexpr (P < 4) {
+        const U32x4 w = philox4x32_10_fixed(k, nl.r1[0], keys);
+        const bool high = (u0 & 2) != 0;
+        Real c, s;
+        box_muller_polar<Real>(high ? w.z : w.x, high ? w.w : w.y, amp[0], c, s);
+        trig[0] = (P == 1 && (u0 & 1)) ? s : c;
+        if constexpr (P == 2) trig[1] = s;
     } else {
 #pragma unroll
         for (int blk = 0; blk < P / 4; ++blk) {
-            const U32x4 w = philox4x32_10(k, (uint32_t)(u0 >> 2) + (uint32_t)blk, orbit, 0u, keys);
-            box_muller<Real>(w.x, w.y, z[4 * blk], z[4 * blk + 1]);
-            box_muller<Real>(w.z, w.w, z[4 * blk + 2], z[4 * blk + 3]);
+            const U32x4 w = philox4x32_10_fixed(k, nl.r1[blk], keys);
+            box_muller_polar<Real>(w.x, w.y, amp[2 * blk], trig[4 * blk], trig[4 * blk + 1]);
+            box_muller_polar<Real>(w.z, w.w, amp[2 * blk + 1], trig[4 * blk + 2], trig[4 * blk + 3]);
         }
     }
 }
@@ -132,31 +152,51 @@ __device__ __forceinline__ void draw_normals(Real (&z)[P], uint32_t k, uint32_t 
 // the state, so they are drawn first and their latency overlaps the coupling
 // sums), the coupling sums over the orbit's lanes (RED), and the compensated
 // update of every unit.  Every unit's increment reads only the old state
-// (synchronous update).  With RECORD the normals are also written to zout
-// (the adjoint's replay).
+// (synchronous update).  A model with one additive noise strength for all
+// its units (kSplitNoise) takes each normal as amplitude times sine or
+// cosine, scaled once per pair, so the normal's product folds into the
+// increment's last fused multiply-add.  With RECORD the normals are also
+// written to zout (the adjoint's replay).
 template <class M, typename Real, int P, bool RECORD = false, class RED>
 __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], uint32_t k,
-                                        uint32_t orbit, int u0, int units, const PhiloxKeys &keys, RED &reduce,
-                                        Real (*zout)[P] = nullptr) {
+                                        const NoiseLane<P> &nl, int u0, int units, const PhiloxKeys &keys,
+                                        RED &reduce, Real (*zout)[P] = nullptr) {
     static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
-    Real z[P];
+    Real amp[kNoisePairs<P>], trig[P];
     if constexpr (M::kNoise) {
-        draw_normals<Real, P>(z, k, orbit, u0, keys);
+        draw_noise<Real, P>(amp, trig, k, u0, nl, keys);
     } else {
 #pragma unroll
-        for (int i = 0; i < P; ++i) z[i] = Real(0);
+        for (int j = 0; j < kNoisePairs<P>; ++j) amp[j] = Real(0);
+#pragma unroll
+        for (int i = 0; i < P; ++i) trig[i] = Real(0);
     }
     constexpr int NRA = M::NR > 0 ? M::NR : 1;
     Real red[NRA];
     model.prepare(x, cp, u0, units, red);
     if constexpr (M::NR > 0) reduce(red);
+    if constexpr (M::kSplitNoise) {
+        Real amp_s[kNoisePairs<P>];
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-        Real inc[M::U];
-        model.incr(i, x, red, z[i], inc);
+        for (int j = 0; j < kNoisePairs<P>; ++j) amp_s[j] = model.noise_scaled(amp[j]);
 #pragma unroll
-        for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
-        if constexpr (RECORD) (*zout)[i] = z[i];
+        for (int i = 0; i < P; ++i) {
+            Real inc[M::U];
+            model.incr_split(i, red, amp_s[noise_pair<P>(i)], trig[i], inc);
+#pragma unroll
+            for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
+            if constexpr (RECORD) (*zout)[i] = mul_r(amp[noise_pair<P>(i)], trig[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const Real z = mul_r(amp[noise_pair<P>(i)], trig[i]);
+            Real inc[M::U];
+            model.incr(i, x, red, z, inc);
+#pragma unroll
+            for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
+            if constexpr (RECORD) (*zout)[i] = z;
+        }
     }
 }
 
@@ -303,6 +343,7 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     uint32_t to_ckpt = a.ckpt_every ? a.ckpt_every - (a.k_begin % a.ckpt_every) : 0u;
 
     WarpGroupSum<G> reduce;
+    const NoiseLane<P> noise(gorb, u0, a.keys);
     // Steps run in runs that end at the next frame, checkpoint or k_end, so
     // the step loop itself carries no per-step bookkeeping.  FP32 unrolls two
     // steps (more independent work between the SFU waits); FP64 keeps one,
@@ -321,7 +362,7 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
             else if constexpr (SCHEME == kSchemeImplicit)
                 implicit_step<M, Real, P>(model, x, cp, u0, units, reduce, a.implicit == 1 ? Real(1) : Real(0.5));
             else
-                em_step<M, Real, P>(model, x, cp, k + s, gorb, u0, units, a.keys, reduce);
+                em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
         }
         k += run;
         if (frames != nullptr && (to_frame -= run) == 0) {

@@ -39,6 +39,7 @@ struct KuramotoLane {
     static constexpr int U = 1;
     static constexpr int NR = 2;
     static constexpr bool kNoise = true;
+    static constexpr bool kSplitNoise = !PAPER;  // one noise strength for every unit
     Real omega_dt[P];         // omega_i dt
     Real live[P];             // 1 for the orbit's units, 0 for padding
     Real gsq[PAPER ? P : 1];  // noise strength times sqrt(dt)
@@ -95,17 +96,33 @@ struct KuramotoLane {
         red[1] = S;
     }
 
-    // f dt + g sqrt(dt) N = (K/n) dt (S cos - C sin) + (omega dt + g sqrt(dt) N)
+    // f dt = (K/n) dt (S cos x_i - C sin x_i) + omega_i dt, with (K/n) dt S
+    // and (K/n) dt C formed once per step (the same products for every unit).
+    __device__ __forceinline__ Real drift_dt(int i, const Real (&red)[NR]) const {
+        const Real kS = mul_r(kn_dt, red[1]), kC = mul_r(kn_dt, red[0]);
+        return fma_r(kS, cs[i], fma_r(-kC, sn[i], omega_dt[i]));
+    }
+
+    // f dt + g sqrt(dt) N
     __device__ __forceinline__ void incr(int i, const Real (&x)[U][P], const Real (&red)[NR], Real N,
                                          Real (&inc)[U]) const {
         (void)x;
-        const Real coupling = fma_r(red[1], cs[i], -mul_r(red[0], sn[i]));  // S cos - C sin
-        inc[0] = fma_r(kn_dt, coupling, fma_r(gsq[PAPER ? i : 0], N, omega_dt[i]));
+        const Real kS = mul_r(kn_dt, red[1]), kC = mul_r(kn_dt, red[0]);
+        inc[0] = fma_r(kS, cs[i], fma_r(-kC, sn[i], fma_r(gsq[PAPER ? i : 0], N, omega_dt[i])));
+    }
+
+    // The scalar noise strength g sqrt(dt) times a Box-Muller amplitude, once
+    // per pair; the increment is then f dt + (g sqrt(dt) amp) trig.
+    __device__ __forceinline__ Real noise_scaled(Real amp) const { return mul_r(gsq[0], amp); }
+
+    __device__ __forceinline__ void incr_split(int i, const Real (&red)[NR], Real amp_scaled, Real trig,
+                                               Real (&inc)[U]) const {
+        inc[0] = fma_r(amp_scaled, trig, drift_dt(i, red));
     }
 
     __device__ __forceinline__ void drift_incr(int i, const Real (&)[U][P], const Real (&red)[NR],
                                                Real (&inc)[U]) const {
-        inc[0] = fma_r(kn_dt, fma_r(red[1], cs[i], -mul_r(red[0], sn[i])), omega_dt[i]);
+        inc[0] = drift_dt(i, red);
     }
 
     // With c_i = cos z_i, s_i = sin z_i the drift's Jacobian is
@@ -161,6 +178,7 @@ struct FhnLane {
     static constexpr int U = 2;
     static constexpr int NR = 1;
     static constexpr bool kNoise = true;
+    static constexpr bool kSplitNoise = false;
     Real a, b, eps, I, c, gsq, dt, inv_units;
     Real half_gsq2;  // (sigma sqrt(dt))^2 / 2, the Milstein coefficient
 
@@ -264,6 +282,7 @@ struct ScalarLane {
     static constexpr int U = 1;
     static constexpr int NR = 0;
     static constexpr bool kNoise = KIND != 2;
+    static constexpr bool kSplitNoise = false;
     Real rate, gsq, dt, half_gsq2;
 
     // Base of the ODE schemes' stage states: the state itself.
