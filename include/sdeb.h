@@ -95,7 +95,13 @@ enum {
 
 /* Precision.  FP32_KAHAN: float state with a Kahan compensation word per
  * state component, float arithmetic, FP64 time variable.  FP64: double
- * everywhere. */
+ * everywhere.  For the Kuramoto models under Euler-Maruyama (and Milstein)
+ * the FP32 compensation is applied every 4 steps, at step multiples of 4:
+ * in between, each increment enters the compensation word alone (one
+ * rounding at the size of a few increments), and the drift reads the phase
+ * x - c.  A state kept for resuming (after sdeb_integrate_range) is the
+ * pair (x, c); frames, sdeb_read_final and the allocation-free path return
+ * its value x - c. */
 enum { SDEB_FP32_KAHAN = 0, SDEB_FP64 = 1 };
 
 /* Problem flags. */

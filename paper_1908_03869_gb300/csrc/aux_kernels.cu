@@ -68,6 +68,11 @@ __global__ void order_param_kernel(const Real *theta, int64_t orbits, int32_t n,
     }
 }
 
+__global__ void state_value_kernel(const float *x, const float *comp, int64_t count, float *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = state_value(x[i], comp[i]);
+}
+
 unsigned grid_for(int64_t work, int block) {
     int64_t g = (work + block - 1) / block;
     if (g < 1) g = 1;
@@ -99,6 +104,12 @@ cudaError_t launch_normals_fill(uint64_t seed, uint32_t k0, int64_t nk, uint32_t
     else
         normals_fill_kernel<float><<<grid_for(total, 256), 256, 0, s>>>(keys, k0, nk, o0, no, m,
                                                                        static_cast<float *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_value(const float *x, const float *comp, int64_t count, float *dst, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    state_value_kernel<<<grid_for(count, 256), 256, 0, s>>>(x, comp, count, dst);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
 #pragma unroll
             for (int i = 0; i < P; ++i) r[0][i] = reduce_phase(x[0][i], cp[0][i]);
             em_step<M, Real, P, true>(model, x, cp, k, noise, u0, units, a.keys, reduce, &z[0]);
+            if constexpr (M::kDelayedComp) {
+                if (((k + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
+            }
             if (active) {
                 Real *row = seg + ((int64_t)(k - k0) * a.orbits + o) * (2 * n);
                 store_units<Real, 1, P>(row, units, u0, r);

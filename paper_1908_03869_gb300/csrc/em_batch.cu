@@ -67,20 +67,26 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
         if (live) mine = min(mine, min(to_frame, steps - k));
         const uint32_t run = __reduce_min_sync(0xffffffffu, mine);
 #pragma unroll 1
-        for (uint32_t s = 0; s < run; ++s) em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+        for (uint32_t s = 0; s < run; ++s) {
+            em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+            if constexpr (M::kDelayedComp) {
+                if (((k + s + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
+            }
+        }
         k += run;
         if (live) {
+            Real v[1][P];
+            unit_values(x, cp, v);   // the state's value (x - c)
             to_frame -= run;
             if (to_frame == 0) {
                 to_frame = in.stride;
                 if (frames != nullptr)
                     store_units<Real, 1, P>(frames + ((int64_t)(k / in.stride) * in.orbits + it.orbit) * n, units, u0,
-                                            x);
+                                            v);
             }
             if (k == steps) {
-                store_units<Real, 1, P>(xrow, units, u0, x);
-                if constexpr (kKahan) store_units<float, 1, P>(crow, units, u0, cp);
-                flag_nonfinite<Real, P>(a.flags + in.o_off + it.orbit, x, u0, units);
+                store_units<Real, 1, P>(xrow, units, u0, v);
+                flag_nonfinite<Real, P>(a.flags + in.o_off + it.orbit, v, u0, units);
             }
         }
     }

@@ -310,4 +310,26 @@ __device__ __forceinline__ void accumulate(double &x, double & /*comp*/, double 
     x = __dadd_rn(x, inc);
 }
 
+// Kahan compensation applied every kCompPeriod steps (the FP32 phase
+// models).  The state is the pair (x, c) with value x - c, as above; within
+// a period each increment only enters c (c -= inc, one rounding at the
+// magnitude of a few increments, far below x's), and at the end of each
+// period renormalize() moves c into x: t = x - c rounded, and c becomes that
+// rounding's error, (t - x) + c, so the value t - c is unchanged.  Periods
+// end at global step multiples of kCompPeriod, so a run resumed from a
+// stored (x, c) at any step, or replayed from a checkpoint, takes the same
+// roundings.
+constexpr uint32_t kCompPeriod = 4;
+
+__device__ __forceinline__ void accumulate_delayed(float &, float &comp, float inc) { comp = __fsub_rn(comp, inc); }
+
+__device__ __forceinline__ void renormalize(float &x, float &comp) {
+    const float t = __fsub_rn(x, comp);
+    comp = __fadd_rn(__fsub_rn(t, x), comp);
+    x = t;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real state_value(Real x, Real comp) { return x - comp; }
+
 }  // namespace sdeb

@@ -184,7 +184,10 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
             Real inc[M::U];
             model.incr_split(i, red, amp_s[noise_pair<P>(i)], trig[i], inc);
 #pragma unroll
-            for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
+            for (int c = 0; c < M::U; ++c) {
+                if constexpr (M::kDelayedComp) accumulate_delayed(x[c][i], cp[c][i], inc[c]);
+                else accumulate(x[c][i], cp[c][i], inc[c]);
+            }
             if constexpr (RECORD) (*zout)[i] = mul_r(amp[noise_pair<P>(i)], trig[i]);
         }
     } else {
@@ -194,10 +197,34 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
             Real inc[M::U];
             model.incr(i, x, red, z, inc);
 #pragma unroll
-            for (int c = 0; c < M::U; ++c) accumulate(x[c][i], cp[c][i], inc[c]);
+            for (int c = 0; c < M::U; ++c) {
+                if constexpr (M::kDelayedComp) accumulate_delayed(x[c][i], cp[c][i], inc[c]);
+                else accumulate(x[c][i], cp[c][i], inc[c]);
+            }
             if constexpr (RECORD) (*zout)[i] = z;
         }
     }
+}
+
+// End of a compensation period (models with kDelayedComp): every unit's
+// compensation folded into its state.
+template <int U, int P>
+__device__ __forceinline__ void renormalize_units(float (&x)[U][P], float (&cp)[U][P]) {
+#pragma unroll
+    for (int c = 0; c < U; ++c)
+#pragma unroll
+        for (int i = 0; i < P; ++i) renormalize(x[c][i], cp[c][i]);
+}
+template <int U, int P>
+__device__ __forceinline__ void renormalize_units(double (&)[U][P], double (&)[U][P]) {}
+
+// The units' values x - c (what a frame or a final state holds).
+template <typename Real, int U, int P>
+__device__ __forceinline__ void unit_values(const Real (&x)[U][P], const Real (&cp)[U][P], Real (&v)[U][P]) {
+#pragma unroll
+    for (int c = 0; c < U; ++c)
+#pragma unroll
+        for (int i = 0; i < P; ++i) v[c][i] = state_value(x[c][i], cp[c][i]);
 }
 
 // One stage of the classical fourth-order Runge-Kutta step (below): the
@@ -344,31 +371,51 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
 
     WarpGroupSum<G> reduce;
     const NoiseLane<P> noise(gorb, u0, a.keys);
-    // Steps run in runs that end at the next frame, checkpoint or k_end, so
-    // the step loop itself carries no per-step bookkeeping.  FP32 unrolls two
-    // steps (more independent work between the SFU waits); FP64 keeps one,
-    // its registers are already near the limit.
+    // Steps run in runs that end at the next frame, checkpoint or k_end (and,
+    // with the periodic compensation, at the next multiple of kCompPeriod),
+    // so the step loop itself carries no per-step bookkeeping.  FP32 unrolls
+    // two steps (more independent work between the SFU waits); FP64 keeps
+    // one, its registers are already near the limit.
+    constexpr bool kDelayed = SCHEME == kSchemeEm && M::kDelayedComp;
     constexpr int kRunUnroll = kKahan ? 2 : 1;
     uint32_t k = a.k_begin;
     while (k < a.k_end) {
         uint64_t k_stop = a.k_end;
         if (frames != nullptr) k_stop = min(k_stop, (uint64_t)k + to_frame);
         if (ckpt != nullptr) k_stop = min(k_stop, (uint64_t)k + to_ckpt);
+        if constexpr (kDelayed) k_stop = min(k_stop, (uint64_t)((k | (kCompPeriod - 1u)) + 1u));
         const uint32_t run = (uint32_t)(k_stop - k);
-#pragma unroll kRunUnroll
-        for (uint32_t s = 0; s < run; ++s) {
-            if constexpr (SCHEME == kSchemeRk4)
-                rk4_step<M, Real, P>(model, x, cp, u0, units, reduce);
-            else if constexpr (SCHEME == kSchemeImplicit)
-                implicit_step<M, Real, P>(model, x, cp, u0, units, reduce, a.implicit == 1 ? Real(1) : Real(0.5));
-            else
+        if (kDelayed && run == kCompPeriod) {
+#pragma unroll 2
+            for (uint32_t s = 0; s < kCompPeriod; ++s)
                 em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+        } else {
+#pragma unroll kRunUnroll
+            for (uint32_t s = 0; s < run; ++s) {
+                if constexpr (SCHEME == kSchemeRk4)
+                    rk4_step<M, Real, P>(model, x, cp, u0, units, reduce);
+                else if constexpr (SCHEME == kSchemeImplicit)
+                    implicit_step<M, Real, P>(model, x, cp, u0, units, reduce, a.implicit == 1 ? Real(1) : Real(0.5));
+                else
+                    em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+            }
         }
         k += run;
+        if constexpr (kDelayed) {
+            if ((k & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
+        }
         if (frames != nullptr && (to_frame -= run) == 0) {
             to_frame = a.stride;
             const int64_t f = (int64_t)(k / a.stride);
-            if (active) store_units<Real, U, P>(frames + (f * a.orbits + o) * n, units, u0, x);
+            if (active) {
+                if constexpr (kDelayed) {
+                    Real v[U][P];
+                    unit_values(x, cp, v);
+                    store_units<Real, U, P>(frames + (f * a.orbits + o) * n, units, u0, v);
+                } else {
+                    store_units<Real, U, P>(frames + (f * a.orbits + o) * n, units, u0, x);
+                }
+            }
         }
         if (ckpt != nullptr && (to_ckpt -= run) == 0) {
             to_ckpt = a.ckpt_every;
@@ -381,13 +428,27 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
         }
     }
 
-    // final state, compensation and the non-finite flag
+    // final state, compensation and the non-finite flag (a state stored for
+    // resuming keeps its pair (x, c); final_value stores the value x - c)
+    if constexpr (kDelayed) {
+        if (a.final_value) {
+            Real v[U][P];
+            unit_values(x, cp, v);
+#pragma unroll
+            for (int c = 0; c < U; ++c)
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    x[c][i] = v[c][i];
+                    cp[c][i] = Real(0);
+                }
+        }
+    }
     bool bad = false;
 #pragma unroll
     for (int c = 0; c < U; ++c)
 #pragma unroll
         for (int i = 0; i < P; ++i)
-            if (u0 + i < units && !isfinite(x[c][i])) bad = true;
+            if (u0 + i < units && !isfinite(state_value(x[c][i], cp[c][i]))) bad = true;
     const unsigned ballot = __ballot_sync(0xffffffffu, bad);
     const int lane = threadIdx.x & 31;
     unsigned group_bits;

@@ -60,7 +60,18 @@ struct ForwardArgs {
     int32_t milstein;  // 1: Milstein step (models with multiplicative noise), 0: Euler-Maruyama
     int32_t rk4;       // 1: fourth-order Runge-Kutta on the drift alone (launch_forward_rk4_*)
     int32_t implicit;  // 1: implicit Euler, 2: implicit midpoint on the drift alone (launch_forward_implicit_*)
+    int32_t final_value;  // 1: leave the state's value x - c in x at k_end (no later resume)
 };
+
+// True when the forward kernel of a problem keeps its FP32 phase states with
+// the compensation folded in every kCompPeriod steps: x alone is then not the
+// state's value between periods (sdeb_read_final returns x - c).
+inline bool delayed_compensation(int32_t model, int32_t precision, uint32_t flags) {
+    return precision == SDEB_FP32_KAHAN && (model == kKuramoto || model == kKuramotoPaper) &&
+           !(flags & (SDEB_FLAG_RK4 | SDEB_FLAG_IMPLICIT_EULER | SDEB_FLAG_IMPLICIT_MIDPOINT));
+}
+// dst[i] = x[i] - comp[i] (FP32), count elements, on the stream (aux_kernels.cu).
+cudaError_t launch_state_value(const float *x, const float *comp, int64_t count, float *dst, cudaStream_t s);
 
 // Returns cudaSuccess or the launch error; cudaErrorNotSupported when the
 // (model, precision, layout) combination has no instantiation.

@@ -40,6 +40,9 @@ struct KuramotoLane {
     static constexpr int NR = 2;
     static constexpr bool kNoise = true;
     static constexpr bool kSplitNoise = !PAPER;  // one noise strength for every unit
+    // FP32: compensation folded into x every kCompPeriod steps (the phase
+    // the drift reads is x - c, formed anyway by the phase reduction)
+    static constexpr bool kDelayedComp = sizeof(Real) == 4;
     Real omega_dt[P];         // omega_i dt
     Real live[P];             // 1 for the orbit's units, 0 for padding
     Real gsq[PAPER ? P : 1];  // noise strength times sqrt(dt)
@@ -179,6 +182,7 @@ struct FhnLane {
     static constexpr int NR = 1;
     static constexpr bool kNoise = true;
     static constexpr bool kSplitNoise = false;
+    static constexpr bool kDelayedComp = false;
     Real a, b, eps, I, c, gsq, dt, inv_units;
     Real half_gsq2;  // (sigma sqrt(dt))^2 / 2, the Milstein coefficient
 
@@ -283,6 +287,7 @@ struct ScalarLane {
     static constexpr int NR = 0;
     static constexpr bool kNoise = KIND != 2;
     static constexpr bool kSplitNoise = false;
+    static constexpr bool kDelayedComp = false;
     Real rate, gsq, dt, half_gsq2;
 
     // Base of the ODE schemes' stage states: the state itself.

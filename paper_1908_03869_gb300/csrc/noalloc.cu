@@ -211,6 +211,7 @@ extern "C" sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void
     a.milstein = (pb->flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     a.rk4 = (pb->flags & SDEB_FLAG_RK4) ? 1 : 0;
     a.implicit = implicit_kind(pb->flags);
+    a.final_value = 1;   // no resume on this path: x_final gets the state's value
     e = launch_forward_any(a, layout, fp64, s);
     if (e == cudaErrorNotSupported) return fail(SDEB_EUNSUPPORTED, "no kernel for this model and layout");
     if (e != cudaSuccess) return fail(SDEB_ECUDA, "forward kernel launch failed");

@@ -904,7 +904,26 @@ sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t 
     const size_t bytes = (size_t)ctx->pb.orbits * ctx->pb.n * ctx->elem;
     if (dst_bytes != bytes) return fail(ctx, SDEB_EINVAL, "dst_bytes=%zu, expected %zu", dst_bytes, bytes);
     const cudaStream_t s = as_stream(stream);
-    cudaError_t e = read_copy(dst, ctx->d_x, bytes, dst_on_device, s);
+    cudaError_t e;
+    if (!ctx->rtc && delayed_compensation(ctx->pb.model, ctx->pb.precision, ctx->pb.flags)) {
+        // the stored pair (x, c) of a resumable state: its value is x - c
+        const int64_t count = ctx->pb.orbits * ctx->pb.n;
+        if (dst_on_device == SDEB_MEM_DEVICE) {
+            e = launch_state_value(static_cast<const float *>(ctx->d_x), ctx->d_comp, count, static_cast<float *>(dst), s);
+        } else {
+            void *tmp = nullptr;
+            e = cudaMallocAsync(&tmp, bytes, s);
+            if (e == cudaSuccess)
+                e = launch_state_value(static_cast<const float *>(ctx->d_x), ctx->d_comp, count, static_cast<float *>(tmp), s);
+            if (e == cudaSuccess) e = read_copy(dst, tmp, bytes, dst_on_device, s);
+            if (tmp) {
+                cudaError_t ef = cudaFreeAsync(tmp, s);
+                if (e == cudaSuccess) e = ef;
+            }
+        }
+    } else {
+        e = read_copy(dst, ctx->d_x, bytes, dst_on_device, s);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(ctx, e, "sdeb_read_final copy");
