@@ -561,6 +561,7 @@ def _time_adjoint(stream, samples, reps=5):
             it.set_params(pt, xt, stream=stream)
             it.autotune(trial_steps=64, stream=stream)
         lay, fwd_lay = ck.layout(), plain.layout()
+        ck_int = sdeb.sdeb_get_checkpoint_interval(ck.ctx)
         ck.integrate(stream=stream)
         xK = ck.final(stream=stream)
         r = torch.empty(orbits, dtype=torch.float32, device="cuda")
@@ -608,7 +609,7 @@ def _time_adjoint(stream, samples, reps=5):
                               "W": W, "orbits": orbits}
     units = orbits * W["steps"]
     return {"workload": "kuramoto n=32, 16384 orbits, shared params, dt=0.01, 2000 steps, ckpt every 100, fp32",
-            "layout_G_P": list(lay), "fwd_layout_G_P": list(fwd_lay),
+            "layout_G_P": list(lay), "fwd_layout_G_P": list(fwd_lay), "ckpt_interval": ck_int,
             "fwd_ms": t_plain, "fwd_ckpt_ms": t_fwd, "adjoint_ms": t_adj,
             "fwd_plus_adjoint_orbit_steps_per_sec": units / ((t_fwd + t_adj) / 1e3),
             "fwd_orbit_steps_per_sec": units / (t_plain / 1e3),

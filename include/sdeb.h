@@ -155,7 +155,8 @@ typedef struct {
     int64_t stride;       /* output every `stride` steps, >= 1 */
     uint64_t seed;        /* Philox key */
     int32_t precision;    /* SDEB_FP32_KAHAN or SDEB_FP64 */
-    int32_t ckpt_every;   /* > 0: keep checkpoints every ckpt_every steps (needed by sdeb_grad) */
+    int32_t ckpt_every;   /* > 0: keep checkpoints at most ckpt_every steps apart (needed by sdeb_grad;
+                             see sdeb_get_checkpoint_interval) */
     uint32_t flags;       /* SDEB_FLAG_* */
     uint32_t reserved;    /* must be 0 */
     int64_t orbit_offset; /* global index of orbit 0 (Philox keying); offset + orbits <= 2^32 */
@@ -376,6 +377,20 @@ SDEB_API sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *b
  * EUNSUPPORTED if the model has no kernel for that layout.  sdeb_create
  * picks a default; sdeb_autotune times the candidates. */
 SDEB_API sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int32_t units_per_lane);
+
+/* The checkpoint interval a context keeps (0 without checkpoints, and for a
+ * batch).  For sdeb_grad the adjoint replays each segment between two
+ * checkpoints into a buffer of phases, normals and coupling sums (2 n + 2
+ * values per orbit and step) that its reverse sweep reads back; when that
+ * buffer, for all orbits resident on the GPU at once, would outgrow half the
+ * L2 cache, sdeb_create keeps checkpoints more often than ckpt_every -- every
+ * ceil(ckpt_every / m) steps, m <= 16, rounded down to a multiple of 4 above
+ * 4 -- so the buffer stays on chip instead of making a round trip through
+ * HBM.  Checkpoint memory is
+ * (steps / interval + 1) x orbits x n elements (FP32: twice that, with the
+ * compensation words).  Gradients do not depend on the interval beyond
+ * rounding. */
+SDEB_API sdeb_status sdeb_get_checkpoint_interval(const sdeb_ctx *ctx, int64_t *steps);
 SDEB_API sdeb_status sdeb_get_layout(const sdeb_ctx *ctx, int32_t *lanes_per_orbit, int32_t *units_per_lane);
 
 /* Layout tuner (motivated by the hand-tuned work-group sizes of the paper's

@@ -25,7 +25,7 @@ __all__ = [
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_frame_moments", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
-    "sdeb_integrate_noalloc", "sdeb_pipe_rate", "sdeb_set_layout", "sdeb_get_layout", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
+    "sdeb_integrate_noalloc", "sdeb_pipe_rate", "sdeb_set_layout", "sdeb_get_layout", "sdeb_get_checkpoint_interval", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
     "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "sdeb_batch_plan", "model_shape",
     "sdeb_swarm_expand", "sdeb_swarm_fitness", "sdeb_swarm_update", "SDEB_SWARM_MAX_DIMS", "PIPES",
     "SDEB_MEM_HOST", "SDEB_MEM_DEVICE", "SDEB_MEM_HOST_ASYNC",
@@ -122,6 +122,7 @@ _SIGS = {
     "sdeb_pipe_rate": (_ST, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
     "sdeb_set_layout": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sdeb_get_layout": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "sdeb_get_checkpoint_interval": (_ST, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "sdeb_autotune": (_ST, [_P, ctypes.c_int64, _P]),
     "sdeb_create_batch": (_ST, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "sdeb_create_user": (_ST, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
@@ -295,6 +296,12 @@ def sdeb_get_layout(ctx):
     g, p = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().sdeb_get_layout(ctx, ctypes.byref(g), ctypes.byref(p)), ctx)
     return g.value, p.value
+
+
+def sdeb_get_checkpoint_interval(ctx):
+    v = ctypes.c_int64()
+    _check(lib().sdeb_get_checkpoint_interval(ctx, ctypes.byref(v)), ctx)
+    return v.value
 
 
 def sdeb_last_error(ctx=None):

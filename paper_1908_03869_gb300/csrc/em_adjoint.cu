@@ -20,8 +20,10 @@
 // pass stored every ckpt_every steps, with the same step code (bit-identical
 // trajectory).  The forward pass stores no noise: the replay regenerates the
 // Philox normals of each step (they drive the recomputed states), and keeps
-// them, with the step's reduced phase (FP32: x - c folded into [-pi, pi]),
-// in a segment buffer that the reverse sweep of the same segment reads back.
+// them, with the step's reduced phase (FP32: x - c folded into [-pi, pi])
+// and the orbit's coupling sums C and S, in a segment buffer that the
+// reverse sweep of the same segment reads back (the sweep takes sin and cos
+// of the phase again, but not C and S).
 #include <type_traits>
 
 #include "em_forward_impl.cuh"
@@ -65,6 +67,8 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
 
     const Real *ckpt = static_cast<const Real *>(a.ckpt);
     Real *seg = static_cast<Real *>(a.seg);
+    // after the [ckpt_every][orbits][2n] phase and normal rows: [ckpt_every][orbits][2] sums
+    Real *seg_sums = seg + (int64_t)a.ckpt_every * a.orbits * (2 * n);
     WarpGroupSum<G> reduce;
     const NoiseLane<P> noise(gorb, u0, a.keys);
     const int64_t nseg = ((int64_t)a.steps + a.ckpt_every - 1) / a.ckpt_every;
@@ -82,26 +86,32 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             for (int i = 0; i < P; ++i) cp[0][i] = Real(0);
         }
         for (uint32_t k = k0; k < k1; ++k) {
-            Real r[1][P], z[1][P];
-#pragma unroll
-            for (int i = 0; i < P; ++i) r[0][i] = reduce_phase(x[0][i], cp[0][i]);
-            em_step<M, Real, P, true>(model, x, cp, k, noise, u0, units, a.keys, reduce, &z[0]);
+            StepRecord<Real, P> rec;
+            em_step<M, Real, P, true>(model, x, cp, k, noise, u0, units, a.keys, reduce, &rec);
             if constexpr (M::kDelayedComp) {
                 if (((k + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
             }
             if (active) {
-                Real *row = seg + ((int64_t)(k - k0) * a.orbits + o) * (2 * n);
-                store_units<Real, 1, P>(row, units, u0, r);
-                store_units<Real, 1, P>(row + n, units, u0, z);
+                const int64_t rowi = (int64_t)(k - k0) * a.orbits + o;
+                Real *row = seg + rowi * (2 * n);
+                store_units<Real, 1, P>(row, units, u0, *reinterpret_cast<const Real(*)[1][P]>(&rec.phase));
+                store_units<Real, 1, P>(row + n, units, u0, *reinterpret_cast<const Real(*)[1][P]>(&rec.z));
+                if (lig == 0) {
+                    seg_sums[2 * rowi] = rec.sums[0];
+                    seg_sums[2 * rowi + 1] = rec.sums[1];
+                }
             }
         }
         // ---- reverse sweep ---------------------------------------------------
         // the next row (step k - 1) is loaded while step k is processed
-        Real rn[1][P], zn[1][P];
+        Real rn[1][P], zn[1][P], Cn, Sn;
         {
-            const Real *row = seg + ((int64_t)(k1 - 1 - k0) * a.orbits + o) * (2 * n);
+            const int64_t rowi = (int64_t)(k1 - 1 - k0) * a.orbits + o;
+            const Real *row = seg + rowi * (2 * n);
             load_units<Real, 1, P>(row, units, u0, rn);
             load_units<Real, 1, P>(row + n, units, u0, zn);
+            Cn = seg_sums[2 * rowi];
+            Sn = seg_sums[2 * rowi + 1];
         }
         for (uint32_t kk = k1; kk > k0; --kk) {
             const uint32_t k = kk - 1;
@@ -111,26 +121,26 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
                 r[0][i] = rn[0][i];
                 z[0][i] = zn[0][i];
             }
+            const Real C = Cn, S = Sn;
             if (k > k0) {
-                const Real *row = seg + ((int64_t)(k - 1 - k0) * a.orbits + o) * (2 * n);
+                const int64_t rowi = (int64_t)(k - 1 - k0) * a.orbits + o;
+                const Real *row = seg + rowi * (2 * n);
                 load_units<Real, 1, P>(row, units, u0, rn);
                 load_units<Real, 1, P>(row + n, units, u0, zn);
+                Cn = seg_sums[2 * rowi];
+                Sn = seg_sums[2 * rowi + 1];
             }
-            // Padding units: live = 0 keeps them out of C and S, and their
-            // lambda stays 0 (it starts at 0 and its update is scaled by
-            // live), so they add nothing to A, B or the gradients.
+            // Padding units: their lambda stays 0 (it starts at 0 and its
+            // update is scaled by live), so they add nothing to A, B or the
+            // gradients; C and S are the replay's, padding already excluded.
             Real sn[P], cs[P];
-            Real C = 0, S = 0, A = 0, B = 0;
+            Real A = 0, B = 0;
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 sincos_reduced(r[0][i], sn[i], cs[i]);
-                C = fma_r(model.live[i], cs[i], C);
-                S = fma_r(model.live[i], sn[i], S);
                 A = fma_r(lam[0][i], cs[i], A);
                 B = fma_r(lam[0][i], sn[i], B);
             }
-            C = group_sum<G>(C);
-            S = group_sum<G>(S);
             A = group_sum<G>(A);
             B = group_sum<G>(B);
 #pragma unroll

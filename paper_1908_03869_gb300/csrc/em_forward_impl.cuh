@@ -155,12 +155,21 @@ __device__ __forceinline__ void draw_noise(Real (&amp)[kNoisePairs<P>], Real (&t
 // (synchronous update).  A model with one additive noise strength for all
 // its units (kSplitNoise) takes each normal as amplitude times sine or
 // cosine, scaled once per pair, so the normal's product folds into the
-// increment's last fused multiply-add.  With RECORD the normals are also
-// written to zout (the adjoint's replay).
+// increment's last fused multiply-add.  With RECORD the step's phases,
+// normals and coupling sums go to rec (the adjoint's replay).
+// What the adjoint's replay keeps of a step (phase models): the reduced
+// phase and the normal of each unit, and the orbit's coupling sums C, S.
+template <typename Real, int P>
+struct StepRecord {
+    Real phase[P];
+    Real z[P];
+    Real sums[2];
+};
+
 template <class M, typename Real, int P, bool RECORD = false, class RED>
 __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], uint32_t k,
                                         const NoiseLane<P> &nl, int u0, int units, const PhiloxKeys &keys,
-                                        RED &reduce, Real (*zout)[P] = nullptr) {
+                                        RED &reduce, StepRecord<Real, P> *rec = nullptr) {
     static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
     Real amp[kNoisePairs<P>], trig[P];
     if constexpr (M::kNoise) {
@@ -175,6 +184,12 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
     Real red[NRA];
     model.prepare(x, cp, u0, units, red);
     if constexpr (M::NR > 0) reduce(red);
+    if constexpr (RECORD) {
+        rec->sums[0] = red[0];
+        rec->sums[1] = red[1];
+#pragma unroll
+        for (int i = 0; i < P; ++i) rec->phase[i] = model.rph[i];
+    }
     if constexpr (M::kSplitNoise) {
         Real amp_s[kNoisePairs<P>];
 #pragma unroll
@@ -188,7 +203,7 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
                 if constexpr (M::kDelayedComp) accumulate_delayed(x[c][i], cp[c][i], inc[c]);
                 else accumulate(x[c][i], cp[c][i], inc[c]);
             }
-            if constexpr (RECORD) (*zout)[i] = mul_r(amp[noise_pair<P>(i)], trig[i]);
+            if constexpr (RECORD) rec->z[i] = mul_r(amp[noise_pair<P>(i)], trig[i]);
         }
     } else {
 #pragma unroll
@@ -201,7 +216,7 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
                 if constexpr (M::kDelayedComp) accumulate_delayed(x[c][i], cp[c][i], inc[c]);
                 else accumulate(x[c][i], cp[c][i], inc[c]);
             }
-            if constexpr (RECORD) (*zout)[i] = z;
+            if constexpr (RECORD) rec->z[i] = z;
         }
     }
 }

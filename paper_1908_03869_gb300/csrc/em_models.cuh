@@ -74,12 +74,17 @@ struct KuramotoLane {
     }
 
     // Padding units enter the sums with weight 0: fma(1, v, s) == s + v.
+    // rph: the phases x - c reduced to [-pi, pi] (FP32) that sin and cos were
+    // taken of, kept for the adjoint's replay record.
+    Real rph[P];
+
     __device__ __forceinline__ void prepare(const Real (&x)[U][P], const Real (&cp)[U][P], int, int,
                                             Real (&red)[NR]) {
         Real C = 0, S = 0;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-            sincos_phase(x[0][i], cp[0][i], sn[i], cs[i]);
+            rph[i] = reduce_phase(x[0][i], cp[0][i]);
+            sincos_reduced(rph[i], sn[i], cs[i]);
             C = fma_r(live[i], cs[i], C);
             S = fma_r(live[i], sn[i], S);
         }

@@ -33,6 +33,7 @@ struct sdeb_ctx {
     void *d_ckpt = nullptr;
     float *d_ckpt_comp = nullptr;
     int64_t nckpt = 0;
+    int64_t ckpt_int = 0;         // checkpoint interval kept (<= pb.ckpt_every; see checkpoint_interval)
     uint8_t *d_flags = nullptr;
     void *d_seg = nullptr;        // adjoint: replayed phases and normals of one segment
     void *d_gradp = nullptr;      // adjoint: per-orbit parameter gradients (shared params)
@@ -663,16 +664,52 @@ sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source, sdeb_ct
 
 namespace {
 
+// Checkpoint interval of a context that keeps checkpoints for sdeb_grad.
+// The adjoint replays one segment (the steps between two checkpoints) into a
+// buffer of phases and normals, 2 n elements per orbit and step, that its
+// reverse sweep reads back; with every resident orbit's segment at once in
+// flight, a segment of ckpt_every steps can outgrow the L2 cache and make
+// the buffer an HBM round trip.  The interval is then cut to ckpt_every / m
+// (m <= 16, so at most 16x the checkpoints asked for) until the in-flight
+// buffer fits a third of the L2.
+int64_t checkpoint_interval(const sdeb_problem *pb, int32_t units, size_t elem, int device) {
+    const int64_t every = pb->ckpt_every;
+    const bool adjoint = every > 0 && (pb->model == SDEB_KURAMOTO || pb->model == SDEB_KURAMOTO_PAPER);
+    if (!adjoint) return every;
+    int l2 = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || l2 <= 0 || sms <= 0) {
+        cudaGetLastError();
+        return every;
+    }
+    Layout l;
+    default_layout(units, l);
+    const int64_t resident = std::min<int64_t>(pb->orbits, (int64_t)sms * 2048 / l.G);
+    const double per_step = (double)resident * (pb->n + 1) * 2.0 * (double)elem;
+    const int64_t fit = std::max<int64_t>(1, (int64_t)((double)l2 / 2.0 / per_step));
+    if (fit >= every) return every;
+    const int64_t m = std::min<int64_t>(16, (every + fit - 1) / fit);
+    int64_t interval = (every + m - 1) / m;
+    // a multiple of 4 when possible: the FP32 forward's compensation periods
+    // then never split at a checkpoint
+    if (interval > 4) interval -= interval % 4;
+    return interval;
+}
+
 sdeb_status create_context(const sdeb_problem *pb, int32_t units, sdeb_ctx **out) {
     const size_t elem = pb->precision == SDEB_FP64 ? 8 : 4;
     const bool shared = pb->flags & SDEB_FLAG_SHARED_PARAMS;
     int64_t state_elems, param_elems, frame_elems = 0, ckpt_elems = 0, seg_elems = 0, gradp_elems = 0;
     const bool adjoint = pb->ckpt_every > 0 && (pb->model == SDEB_KURAMOTO || pb->model == SDEB_KURAMOTO_PAPER);
+    int device = 0;
+    cudaError_t e0 = cudaGetDevice(&device);
+    if (e0 != cudaSuccess) return cuda_fail(nullptr, e0, "cudaGetDevice");
+    const int64_t ckpt_int = checkpoint_interval(pb, units, elem, device);
     int64_t nframes = (pb->flags & SDEB_FLAG_NO_FRAMES) ? 0 : pb->steps / pb->stride + 1;
-    int64_t nckpt = pb->ckpt_every > 0 ? (pb->steps + pb->ckpt_every - 1) / pb->ckpt_every + 1 : 0;
+    int64_t nckpt = ckpt_int > 0 ? (pb->steps + ckpt_int - 1) / ckpt_int + 1 : 0;
     if (!mul_ok(pb->orbits, pb->n, state_elems) || !mul_ok(shared ? 1 : pb->orbits, pb->d, param_elems) ||
         !mul_ok(nframes, state_elems, frame_elems) || !mul_ok(nckpt, state_elems, ckpt_elems) ||
-        !mul_ok(adjoint ? 2 * (int64_t)pb->ckpt_every : 0, state_elems, seg_elems) ||
+        !mul_ok(adjoint ? 2 * ckpt_int : 0, state_elems + pb->orbits, seg_elems) ||
         !mul_ok(adjoint && shared ? pb->orbits : 0, pb->d, gradp_elems) ||
         frame_elems > INT64_MAX / 8 || ckpt_elems > INT64_MAX / 8 || seg_elems > INT64_MAX / 8)
         return fail(nullptr, SDEB_EINVAL, "problem size overflows");
@@ -684,13 +721,10 @@ sdeb_status create_context(const sdeb_problem *pb, int32_t units, sdeb_ctx **out
     c->elem = elem;
     c->nframes = nframes;
     c->nckpt = nckpt;
+    c->ckpt_int = ckpt_int;
     default_layout(units, c->layout);
-
-    cudaError_t e = cudaGetDevice(&c->device);
-    if (e != cudaSuccess) {
-        delete c;
-        return cuda_fail(nullptr, e, "cudaGetDevice");
-    }
+    c->device = device;
+    cudaError_t e = cudaSuccess;
     c->params_bytes = (size_t)param_elems * elem;
     struct {
         void **p;
@@ -838,7 +872,7 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
     a.nframes = ctx->nframes;
     a.ckpt = ctx->d_ckpt;
     a.ckpt_comp = ctx->d_ckpt_comp;
-    a.ckpt_every = (uint32_t)ctx->pb.ckpt_every;
+    a.ckpt_every = (uint32_t)ctx->ckpt_int;
     a.k_begin = (uint32_t)k_begin;
     a.k_end = (uint32_t)k_end;
     a.stride = (uint32_t)ctx->pb.stride;
@@ -1025,13 +1059,21 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
         return fail(ctx, SDEB_ESTATE, "call sdeb_autotune after sdeb_set_params and before integrating");
     if (ctx->rtc) return SDEB_OK;  // a user model has one kernel shape: one thread per orbit
     // A context that keeps checkpoints for sdeb_grad is tuned for forward +
-    // adjoint: both are timed over one segment (at most 1024 steps) from
-    // checkpoint 0, which sdeb_set_params has written.
+    // adjoint, each timed per step: the forward over trial_steps steps, the
+    // adjoint over whole segments covering at least 64 steps (at most 1024)
+    // from checkpoints that are copies of checkpoint 0 (the one
+    // sdeb_set_params has written; the integration overwrites them).
     const bool tune_adjoint = ctx->d_seg != nullptr && !(ctx->pb.flags & (kSchemeFlags));
     if (trial_steps <= 0) trial_steps = 64;
-    if (tune_adjoint) trial_steps = std::min<int64_t>((int64_t)ctx->pb.ckpt_every, 1024);
+    if (tune_adjoint) trial_steps = std::min<int64_t>(std::max<int64_t>(trial_steps, 64), 1024);
     if (trial_steps > ctx->pb.steps) trial_steps = ctx->pb.steps;
     if (trial_steps == 0) return SDEB_OK;
+    int64_t adj_steps = 0;
+    if (tune_adjoint) {
+        const int64_t segs = std::max<int64_t>(1, std::min<int64_t>(1024, std::max<int64_t>(64, ctx->ckpt_int)) /
+                                                      ctx->ckpt_int);
+        adj_steps = std::min<int64_t>(segs * ctx->ckpt_int, ctx->pb.steps);
+    }
     static const Layout kCandidates[] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 4}, {2, 8}, {4, 4}, {4, 8}, {4, 16},
                                          {8, 4}, {8, 8}, {8, 16}, {16, 4}, {16, 8}, {32, 4}, {32, 8}};
     const cudaStream_t s = as_stream(stream);
@@ -1098,8 +1140,8 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
             g.param_stride = a.param_stride;
             g.ckpt = ctx->d_ckpt;
             g.ckpt_comp = ctx->d_ckpt_comp;
-            g.ckpt_every = (uint32_t)ctx->pb.ckpt_every;
-            g.steps = (uint32_t)trial_steps;
+            g.ckpt_every = (uint32_t)ctx->ckpt_int;
+            g.steps = (uint32_t)adj_steps;
             g.orbit_offset = a.orbit_offset;
             g.dt = ctx->pb.dt;
             g.seg = ctx->d_seg;
@@ -1107,6 +1149,15 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
             g.dL_dp = t_dp;
             g.keys = a.keys;
             float ms_adj = 0.0f;
+            // checkpoints 1 .. of the trial: copies of checkpoint 0
+            const int64_t ck_used = (adj_steps + ctx->ckpt_int - 1) / ctx->ckpt_int;
+            for (int64_t c = 1; c < ck_used && e == cudaSuccess; ++c) {
+                e = cudaMemcpyAsync(static_cast<char *>(ctx->d_ckpt) + c * state_bytes, ctx->d_ckpt, state_bytes,
+                                    cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess && ctx->d_ckpt_comp)
+                    e = cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_ckpt_comp) + c * ((size_t)ctx->pb.orbits *
+                                        ctx->pb.n * 4), 0, (size_t)ctx->pb.orbits * ctx->pb.n * 4, s);
+            }
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                 e = cudaEventRecord(e0, s);
                 if (e == cudaSuccess) e = launch_adjoint(g, l, ctx->pb.precision == SDEB_FP64, s);
@@ -1114,7 +1165,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_adj, e0, e1);
             }
-            ms += ms_adj;
+            ms = ms / (float)trial_steps + ms_adj / (float)adj_steps;   // per step, forward + adjoint
         }
         if (e == cudaErrorNotSupported) {
             e = cudaSuccess;
@@ -1138,6 +1189,12 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
         return cuda_fail(ctx, e, "sdeb_autotune");
     }
     ctx->layout = best;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_get_checkpoint_interval(const sdeb_ctx *ctx, int64_t *steps) {
+    if (!ctx || !steps) return fail(nullptr, SDEB_EINVAL, "ctx and steps must not be NULL");
+    *steps = ctx->is_batch ? 0 : ctx->ckpt_int;
     return SDEB_OK;
 }
 
@@ -1181,7 +1238,7 @@ sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_d
     a.param_stride = shared ? 0 : ctx->pb.d;
     a.ckpt = ctx->d_ckpt;
     a.ckpt_comp = ctx->d_ckpt_comp;
-    a.ckpt_every = (uint32_t)ctx->pb.ckpt_every;
+    a.ckpt_every = (uint32_t)ctx->ckpt_int;
     a.steps = (uint32_t)ctx->pb.steps;
     a.orbit_offset = (uint32_t)ctx->pb.orbit_offset;
     a.dt = ctx->pb.dt;

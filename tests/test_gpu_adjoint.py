@@ -89,6 +89,38 @@ def test_adjoint_matches_oracle(precision, model, n, ckpt):
     assert _rel(dx0, rdx0) < tol
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_with_a_shortened_checkpoint_interval(precision):
+    """Many orbits of n = 128: the segment buffer for ckpt_every = 97 would
+    outgrow a third of the L2, so the context keeps checkpoints more often
+    (an interval that does not divide the 302 steps: a ragged last
+    segment).  Sampled orbits' gradients against the oracle adjoint."""
+    import torch
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    n, orbits, dt, steps, ckpt, seed = 128, 8192, 0.01, 302, 97, 6
+    p, x0 = inputs.kuramoto(n, orbits, seed=7)
+    p, x0 = p.astype(np_dtype(precision)).astype(np.float64), x0.astype(np_dtype(precision)).astype(np.float64)
+    c = np.random.Generator(np.random.PCG64(3)).standard_normal((orbits, n))
+    dt_t = torch.float64 if precision == "fp64" else torch.float32
+    pb = sdeb.Problem.make("kuramoto", n, orbits, dt, steps, 1, seed, precision, ckpt_every=ckpt, no_frames=True)
+    with Integrator(pb) as it:
+        interval = sdeb.sdeb_get_checkpoint_interval(it.ctx)
+        it.set_params(torch.tensor(p, dtype=dt_t).cuda(), torch.tensor(x0, dtype=dt_t).cuda())
+        it.integrate()
+        dp, dx0 = it.grad(torch.tensor(c, dtype=dt_t).cuda())
+        dp, dx0 = dp.cpu().numpy(), dx0.cpu().numpy()
+    print("checkpoint interval", interval)
+    assert 0 < interval < ckpt and steps % interval != 0
+    m, d = sdeb.model_shape("kuramoto", n)
+    opb = oracle.make_problem("kuramoto", n, m, d, dt, steps, 1, seed)
+    tol = 1e-10 if precision == "fp64" else 1e-3
+    for o in (0, 4095, 8191):
+        rdp, rdx0 = oracle.adjoint(opb, p[o:o + 1], x0[o:o + 1], c[o:o + 1], orbit_begin=o)
+        assert _rel(dp[o:o + 1], rdp) < tol, o
+        assert _rel(dx0[o:o + 1], rdx0) < tol, o
+
+
 def _loss_and_grads(precision, p, x0, W, steps=None, want_grad=True, shared=True):
     import torch
     from paper_1908_03869_gb300.autograd import integrate_final, order_parameter
