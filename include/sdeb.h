@@ -63,7 +63,8 @@ typedef enum {
     SDEB_ETIMEOUT = 4,      /* a bounded device wait gave up */
     SDEB_ESTATE = 5,        /* call order violated (e.g. read before integrate) */
     SDEB_EUNSUPPORTED = 6,  /* valid request the library does not implement */
-    SDEB_ENONFINITE = 7     /* some orbit left the finite range (see sdeb_orbit_flags) */
+    SDEB_ENONFINITE = 7,    /* some orbit left the finite range (see sdeb_orbit_flags) */
+    SDEB_EBOUNDS = 8        /* the checked build recorded an out-of-range index (sdeb_check_status) */
 } sdeb_status;
 
 /* Models (drift f and diffusion g of Eq. 1). */
@@ -409,6 +410,25 @@ SDEB_API sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *str
 
 SDEB_API const char *sdeb_last_error(const sdeb_ctx *ctx);
 SDEB_API const char *sdeb_status_string(sdeb_status s);
+
+/* ---- Bounds-checked build ------------------------------------------------
+ * No counterpart in the paper.  The same sources compiled with SDEB_CHECKED
+ * give libsdeb_checked.so (paper_1908_03869_gb300.build.build(checked=True);
+ * the Python binding loads it when SDEB_LIBRARY=checked).  Its kernels
+ * compare every run-time row or table index with the extent of the buffer it
+ * addresses -- state rows, frame and checkpoint indices, the adjoint's
+ * segment rows, a batch's task, item and instance tables and packed-warp
+ * lane offsets, a user model's frame index, the moment reduction's frames --
+ * and on a failed check skip the access and record (site << 48 | index) in
+ * one device status word (the first failure wins).  No kernel traps.
+ * sdeb_check_status synchronises the device, returns the word in *word,
+ * clears it, and returns SDEB_EBOUNDS if it was set, SDEB_OK if not;
+ * sdeb_check_selftest enqueues a kernel on `stream` that records site
+ * 0xFFFF, index 12345 through the same path (it touches no other memory), to
+ * test the reporting.  In the unchecked library both return
+ * SDEB_EUNSUPPORTED without a CUDA call. */
+SDEB_API sdeb_status sdeb_check_status(uint64_t *word);
+SDEB_API sdeb_status sdeb_check_selftest(void *stream);
 
 /* ---- Stand-alone kernels of the path (device pointers) ------------------ */
 

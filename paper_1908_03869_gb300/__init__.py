@@ -17,7 +17,7 @@ from . import build as _build
 __all__ = [
     "SdebError", "Problem", "lib", "library_path",
     "SDEB_OK", "SDEB_EINVAL", "SDEB_ENOMEM", "SDEB_ECUDA", "SDEB_ETIMEOUT", "SDEB_ESTATE",
-    "SDEB_EUNSUPPORTED", "SDEB_ENONFINITE",
+    "SDEB_EUNSUPPORTED", "SDEB_ENONFINITE", "SDEB_EBOUNDS", "sdeb_check_status", "sdeb_check_selftest",
     "SDEB_KURAMOTO", "SDEB_KURAMOTO_PAPER", "SDEB_FHN_NET", "SDEB_OU", "SDEB_GBM", "SDEB_LINEAR_ODE",
     "SDEB_USER", "SDEB_USER_MAX_N", "SDEB_USER_MAX_M", "sdeb_create_user",
     "SDEB_FP32_KAHAN", "SDEB_FP64", "SDEB_FLAG_SHARED_PARAMS", "SDEB_FLAG_NO_FRAMES", "SDEB_FLAG_MILSTEIN",
@@ -32,7 +32,8 @@ __all__ = [
     "EXPORTED_SYMBOLS",
 ]
 
-SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE = range(8)
+SDEB_OK, SDEB_EINVAL, SDEB_ENOMEM, SDEB_ECUDA, SDEB_ETIMEOUT, SDEB_ESTATE, SDEB_EUNSUPPORTED, SDEB_ENONFINITE, \
+    SDEB_EBOUNDS = range(9)
 SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER, SDEB_FHN_NET, SDEB_OU, SDEB_GBM, SDEB_LINEAR_ODE, SDEB_USER = range(1, 8)
 SDEB_USER_MAX_N = SDEB_USER_MAX_M = 64
 SDEB_FP32_KAHAN, SDEB_FP64 = 0, 1
@@ -94,7 +95,7 @@ class SdebError(RuntimeError):
 
 
 _STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE",
-                 6: "EUNSUPPORTED", 7: "ENONFINITE"}
+                 6: "EUNSUPPORTED", 7: "ENONFINITE", 8: "EBOUNDS"}
 
 _P = ctypes.c_void_p
 _ST = ctypes.c_int
@@ -120,6 +121,8 @@ _SIGS = {
     "sdeb_order_param": (_ST, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "sdeb_integrate_noalloc": (_ST, [ctypes.POINTER(Problem), _P, _P, _P, _P, _P]),
     "sdeb_pipe_rate": (_ST, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P]),
+    "sdeb_check_status": (_ST, [ctypes.POINTER(ctypes.c_uint64)]),
+    "sdeb_check_selftest": (_ST, [_P]),
     "sdeb_set_layout": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sdeb_get_layout": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sdeb_get_checkpoint_interval": (_ST, [_P, ctypes.POINTER(ctypes.c_int64)]),
@@ -146,7 +149,9 @@ _lib = None
 
 
 def library_path():
-    return _build.LIB_PATH
+    """libsdeb.so, or the bounds-checked libsdeb_checked.so when the
+    environment variable SDEB_LIBRARY is "checked"."""
+    return _build.CHECKED_LIB_PATH if os.environ.get("SDEB_LIBRARY") == "checked" else _build.LIB_PATH
 
 
 def lib():
@@ -346,6 +351,19 @@ def sdeb_swarm_update(x, v, pbest, pbest_fit, fit, particles, lo, hi, w, c1, c2,
         raise ValueError("lo and hi need one bound per dimension")
     _check(lib().sdeb_swarm_update(x, v, pbest, pbest_fit, fit, particles, len(lo), lo_a, hi_a, float(w), float(c1),
                                    float(c2), seed & 0xFFFFFFFFFFFFFFFF, generation, gbest, _stream(stream)))
+
+
+def sdeb_check_status():
+    """(status, word) of the checked build's bounds-check status word (read
+    and cleared); status SDEB_EBOUNDS when a check failed, SDEB_EUNSUPPORTED
+    in the unchecked library."""
+    w = ctypes.c_uint64()
+    st = lib().sdeb_check_status(ctypes.byref(w))
+    return st, w.value
+
+
+def sdeb_check_selftest(stream=None):
+    _check(lib().sdeb_check_selftest(_stream(stream)))
 
 
 PIPES = {"sfu_sin": 0, "sfu_lg2": 1, "sfu_sqrt": 2, "fp64_fma": 3, "fp32_fma": 4}

@@ -19,6 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libsdeb.so"
 LIB_PATH = os.path.join(BUILD_DIR, LIB_NAME)
+# The bounds-checked build: the same sources compiled with SDEB_CHECKED.
+CHECKED_BUILD_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB_PATH = os.path.join(CHECKED_BUILD_DIR, "libsdeb_checked.so")
 
 GEN_DIR = os.path.join(BUILD_DIR, "gen")
 
@@ -28,7 +31,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 
 # Device sources compiled again at run time for user-defined models (NVRTC):
 # embedded into the library as string constants, one per file.
-RTC_EMBED = [("kRtcEmDevice", "em_device.cuh"), ("kRtcArgs", "rtc_args.h"), ("kRtcKernel", "rtc_kernel.cuh")]
+RTC_EMBED = [("kRtcCheck", "check.cuh"), ("kRtcEmDevice", "em_device.cuh"), ("kRtcArgs", "rtc_args.h"),
+             ("kRtcKernel", "rtc_kernel.cuh")]
 RTC_INC = os.path.join(GEN_DIR, "sdeb_rtc_sources.inc")
 
 
@@ -66,16 +70,17 @@ def headers():
     return hs + [os.path.join(INCLUDE, "sdeb.h")]
 
 
-def needs_build():
-    if not os.path.exists(LIB_PATH):
+def needs_build(checked=False):
+    lib = CHECKED_LIB_PATH if checked else LIB_PATH
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in sources() + headers() + [os.path.abspath(__file__)])
 
 
-def _compile(src, verbose_ptxas=False):
-    obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-    cmd = [_nvcc()] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+def _compile(src, verbose_ptxas=False, checked=False):
+    obj = os.path.join(CHECKED_BUILD_DIR if checked else BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+    cmd = [_nvcc()] + ARCH + NVCC_FLAGS + (["-DSDEB_CHECKED=1"] if checked else []) + ["-c", src, "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -84,26 +89,30 @@ def _compile(src, verbose_ptxas=False):
     return obj, r.stderr
 
 
-def build(force=False, verbose_ptxas=False, jobs=None):
-    if not force and not needs_build():
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force=False, verbose_ptxas=False, jobs=None, checked=False):
+    """Build libsdeb.so, or with checked=True the bounds-checked
+    libsdeb_checked.so (every kernel compiled with SDEB_CHECKED)."""
+    lib = CHECKED_LIB_PATH if checked else LIB_PATH
+    if not force and not needs_build(checked):
+        return lib
+    os.makedirs(CHECKED_BUILD_DIR if checked else BUILD_DIR, exist_ok=True)
+    os.makedirs(GEN_DIR, exist_ok=True)
     generate_rtc_sources()
     srcs = sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
+        results = list(ex.map(lambda s: _compile(s, verbose_ptxas, checked), srcs))
     if verbose_ptxas:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-cudart", "static", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, checked="--checked" in sys.argv))

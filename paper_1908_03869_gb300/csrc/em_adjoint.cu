@@ -78,9 +78,19 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
         const uint32_t k1 = (uint32_t)((int64_t)k0 + a.ckpt_every < (int64_t)a.steps ? k0 + a.ckpt_every : a.steps);
         // ---- replay the segment from its checkpoint --------------------------
         Real x[1][P], cp[1][P];
-        load_units<Real, 1, P>(ckpt + (c * a.orbits + o) * n, units, u0, x);
+        if (SDEB_CHECK(a.check, c < a.nckpt, kChkAdjointCkpt, c)) {
+            load_units<Real, 1, P>(ckpt + (c * a.orbits + o) * n, units, u0, x);
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) x[0][i] = Real(0);
+        }
         if constexpr (std::is_same<Real, float>::value) {
-            load_units<float, 1, P>(a.ckpt_comp + (c * a.orbits + o) * n, units, u0, cp);
+            if (c < a.nckpt) {
+                load_units<float, 1, P>(a.ckpt_comp + (c * a.orbits + o) * n, units, u0, cp);
+            } else {
+#pragma unroll
+                for (int i = 0; i < P; ++i) cp[0][i] = 0.0f;
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < P; ++i) cp[0][i] = Real(0);
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             if constexpr (M::kDelayedComp) {
                 if (((k + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
             }
-            if (active) {
+            if (active && SDEB_CHECK(a.check, k - k0 < a.ckpt_every, kChkAdjointSeg, k - k0)) {
                 const int64_t rowi = (int64_t)(k - k0) * a.orbits + o;
                 Real *row = seg + rowi * (2 * n);
                 store_units<Real, 1, P>(row, units, u0, *reinterpret_cast<const Real(*)[1][P]>(&rec.phase));
@@ -105,6 +115,7 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
         // ---- reverse sweep ---------------------------------------------------
         // the next row (step k - 1) is loaded while step k is processed
         Real rn[1][P], zn[1][P], Cn, Sn;
+        (void)SDEB_CHECK(a.check, k1 > k0 && k1 - 1 - k0 < a.ckpt_every, kChkAdjointSeg, k1 - k0);
         {
             const int64_t rowi = (int64_t)(k1 - 1 - k0) * a.orbits + o;
             const Real *row = seg + rowi * (2 * n);
@@ -160,7 +171,7 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
     // per-orbit gradients: p = (K, sigma, omega_1..omega_n) or (K, omega, p_1..p_n)
     g_k = group_sum<G>(g_k);
     if (!PAPER) g_noise[0] = group_sum<G>(g_noise[0]);
-    if (active) {
+    if (active && SDEB_CHECK(a.check, o < a.orbits, kChkAdjointOut, o)) {
         Real *gp = static_cast<Real *>(a.dL_dp) + o * a.d;
         if (lig == 0) {
             gp[0] = g_k * (dt / (Real)units);

@@ -38,6 +38,14 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
     const int u0 = lane * P;
     const int units = in.units;
     const int64_t n = in.n;
+    // the item's rows lie inside the concatenated buffers; its lane offset inside the item
+    (void)SDEB_CHECK(a.check, !has || (it.orbit >= 0 && it.orbit < in.orbits), kChkBatchInstance, it.orbit);
+    (void)SDEB_CHECK(a.check, !has || in.x_off + ((int64_t)it.orbit + 1) * n <= a.state_elems, kChkBatchState,
+                     in.x_off + (int64_t)it.orbit * n);
+    (void)SDEB_CHECK(a.check, !has || in.p_off + (int64_t)it.orbit * in.param_stride + in.d <= a.param_elems,
+                     kChkBatchParams, in.p_off + (int64_t)it.orbit * in.param_stride);
+    (void)SDEB_CHECK(a.check, !has || in.o_off + it.orbit < a.nitems, kChkBatchFlags, in.o_off + it.orbit);
+    (void)SDEB_CHECK(a.check, u0 >= 0 && u0 < 256, kChkBatchLane, u0);
     M model;
     model.load(static_cast<const Real *>(a.params) + in.p_off + (int64_t)it.orbit * in.param_stride, u0, units,
                (Real)in.dt, (Real)sqrt(in.dt));
@@ -80,7 +88,8 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
             to_frame -= run;
             if (to_frame == 0) {
                 to_frame = in.stride;
-                if (frames != nullptr)
+                const int64_t frow = in.f_off + ((int64_t)(k / in.stride) * in.orbits + it.orbit) * n;
+                if (frames != nullptr && SDEB_CHECK(a.check, frow + n <= a.frame_elems, kChkBatchFrame, frow))
                     store_units<Real, 1, P>(frames + ((int64_t)(k / in.stride) * in.orbits + it.orbit) * n, units, u0,
                                             v);
             }
@@ -126,8 +135,11 @@ template <typename Real, int P>
 __device__ __forceinline__ void run_packed_warp(const BatchArgs &a, const BatchWarpTask &t) {
     const int lane = threadIdx.x & 31;
     int start = 0, mine = -1, s = lane, e = lane + 1, longest = 1;
+    if (!SDEB_CHECK(a.check, t.first >= 0 && t.first + t.count <= a.nitems, kChkBatchItem, t.first)) return;
     for (int j = 0; j < t.count; ++j) {
-        const int len = (a.inst[a.items[t.first + j].instance].units + P - 1) / P;
+        const int32_t ins = a.items[t.first + j].instance;
+        if (!SDEB_CHECK(a.check, ins >= 0 && ins < a.ninst, kChkBatchInstance, ins)) return;
+        const int len = (a.inst[ins].units + P - 1) / P;
         if (lane >= start && lane < start + len) {
             mine = j;
             s = start;
@@ -136,6 +148,8 @@ __device__ __forceinline__ void run_packed_warp(const BatchArgs &a, const BatchW
         longest = max(longest, len);
         start += len;
     }
+    // the item's segment [s, e) lies inside the warp (the packing keeps it within 32 lanes)
+    if (!SDEB_CHECK(a.check, s >= 0 && e <= 32 && s < e, kChkBatchLane, (int64_t)s * 64 + e)) return;
     SegmentSum reduce;
     reduce.last = e - 1;
     reduce.levels = 32 - __clz(longest - 1);
@@ -183,7 +197,10 @@ struct NamedTeamSum {
 template <typename Real, int NW, int P, int BAR>
 __device__ __forceinline__ void run_team(const BatchArgs &a, int32_t item, Real *buf, int warp0) {
     NamedTeamSum<NW, BAR, Real> reduce{buf, 0, warp0};
+    // a task's item index comes from the host's table: every thread of the team checks the same value
+    if (!SDEB_CHECK(a.check, item >= 0 && item < a.nitems, kChkBatchItem, item)) return;
     const BatchItem it = a.items[item];
+    if (!SDEB_CHECK(a.check, it.instance >= 0 && it.instance < a.ninst, kChkBatchInstance, it.instance)) return;
     const uint32_t steps = a.inst[it.instance].steps;
     run_item<Real, P>(a, it, true, (int)threadIdx.x - warp0 * 32, steps, reduce);
 }

@@ -24,6 +24,10 @@ typedef unsigned long long uint64_t;
 #include <cuda_runtime.h>
 #endif
 
+#ifndef __CUDACC_RTC__
+#include "check.cuh"  // the run-time compiled path gets it ahead of this header
+#endif
+
 namespace sdeb {
 
 // ---------------------------------------------------------------------------

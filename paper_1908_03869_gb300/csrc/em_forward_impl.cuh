@@ -361,6 +361,9 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     const int u0 = lig * P;
     const int units = a.units;
     const int64_t n = a.n;
+    // o is clamped into [0, orbits) (lanes past the last orbit repeat it and
+    // store nothing): the check records a launch whose orbit count is wrong
+    (void)SDEB_CHECK(a.check, o >= 0 && o < a.orbits, kChkForwardState, o);
 
     M model;
     model.load(static_cast<const Real *>(a.params) + o * a.param_stride, u0, units, (Real)a.dt,
@@ -422,7 +425,7 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
         if (frames != nullptr && (to_frame -= run) == 0) {
             to_frame = a.stride;
             const int64_t f = (int64_t)(k / a.stride);
-            if (active) {
+            if (active && SDEB_CHECK(a.check, f < a.nframes, kChkForwardFrame, f)) {
                 if constexpr (kDelayed) {
                     Real v[U][P];
                     unit_values(x, cp, v);
@@ -435,7 +438,7 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
         if (ckpt != nullptr && (to_ckpt -= run) == 0) {
             to_ckpt = a.ckpt_every;
             const int64_t c = (int64_t)(k / a.ckpt_every);
-            if (active) {
+            if (active && SDEB_CHECK(a.check, c < a.nckpt, kChkForwardCkpt, c)) {
                 store_units<Real, U, P>(ckpt + (c * a.orbits + o) * n, units, u0, x);
                 if constexpr (kKahan)
                     store_units<float, U, P>(a.ckpt_comp + (c * a.orbits + o) * n, units, u0, cp);

@@ -61,7 +61,13 @@ struct ForwardArgs {
     int32_t rk4;       // 1: fourth-order Runge-Kutta on the drift alone (launch_forward_rk4_*)
     int32_t implicit;  // 1: implicit Euler, 2: implicit midpoint on the drift alone (launch_forward_implicit_*)
     int32_t final_value;  // 1: leave the state's value x - c in x at k_end (no later resume)
+    int64_t nckpt;         // checkpoints in ckpt
+    unsigned long long *check;  // bounds-check status word (checked build), or null
 };
+
+// The checked build's device status word on the current device (null in the
+// unchecked build, which compiles no checks).  checked.cu.
+unsigned long long *check_word();
 
 // True when the forward kernel of a problem keeps its FP32 phase states with
 // the compensation folded in every kCompPeriod steps: x alone is then not the
@@ -110,6 +116,8 @@ struct AdjointArgs {
     void *dL_dp;               // [orbits][d]
     void *dL_dx0;              // [orbits][n] or nullptr
     PhiloxKeys keys;
+    int64_t nckpt;             // checkpoints in ckpt
+    unsigned long long *check; // bounds-check status word (checked build), or null
 };
 
 cudaError_t launch_adjoint(const AdjointArgs &a, Layout l, bool fp64, cudaStream_t s);
@@ -173,6 +181,10 @@ struct BatchArgs {
     void *frames;                  // nullptr: no frames (tuning runs)
     uint8_t *flags;
     PhiloxKeys keys;
+    // extents for the checked build's bounds checks
+    int32_t ninst;
+    int64_t nitems, state_elems, frame_elems, param_elems;
+    unsigned long long *check;
 };
 
 cudaError_t launch_batch(const BatchArgs &a, int grid, bool fp64, cudaStream_t s);
@@ -212,7 +224,7 @@ FrameMomentsPlan frame_moments_plan(int64_t orbits, int n, int64_t count);
 // the order parameter of Eq. 7; either may be nullptr.  partial: device
 // scratch of plan.partial_bytes.
 cudaError_t launch_frame_moments_pass(const void *frames, bool fp64, int64_t orbits, int n, int64_t f0,
-                                      int64_t count, const FrameMomentsPlan &plan, void *partial,
+                                      int64_t count, int64_t nframes, const FrameMomentsPlan &plan, void *partial,
                                       double *state_out, double *r_out, cudaStream_t s);
 
 // Auxiliary kernels (aux_kernels.cu).

@@ -66,10 +66,12 @@ __device__ __forceinline__ Acc acc_from_shifted(double cnt, double K, double s1,
 // addresses.
 template <typename Real>
 __global__ void __launch_bounds__(kMomBlock) state_moments_partial(const Real *frames, int64_t orbits, int n,
-                                                                   int64_t f0, int C, Acc *part) {
+                                                                   int64_t f0, int64_t nframes, int C, Acc *part,
+                                                                   unsigned long long *check) {
     __shared__ Acc sh[kMomBlock];
     const int c = (int)(blockIdx.x % (unsigned)C);
     const int64_t fr = blockIdx.x / (unsigned)C;
+    if (!SDEB_CHECK(check, f0 + fr < nframes, kChkMomentFrame, f0 + fr)) return;  // uniform over the block
     const int64_t o0 = (int64_t)c * kMomChunk;
     const int64_t o1 = min(orbits, o0 + kMomChunk);
     const Real *base = frames + (f0 + fr) * orbits * (int64_t)n;
@@ -111,11 +113,13 @@ __global__ void __launch_bounds__(kMomBlock) state_moments_partial(const Real *f
 // warp.
 template <typename Real, int G>
 __global__ void __launch_bounds__(kMomBlock) r_moments_partial(const Real *frames, int64_t orbits, int n,
-                                                               int64_t f0, int C, Acc *part) {
+                                                               int64_t f0, int64_t nframes, int C, Acc *part,
+                                                               unsigned long long *check) {
     constexpr int kGroups = kMomBlock / G;
     __shared__ Acc sh[kGroups];
     const int c = (int)(blockIdx.x % (unsigned)C);
     const int64_t fr = blockIdx.x / (unsigned)C;
+    if (!SDEB_CHECK(check, f0 + fr < nframes, kChkMomentFrame, f0 + fr)) return;  // uniform over the block
     const int64_t o0 = (int64_t)c * kMomChunk;
     const int64_t o1 = min(orbits, o0 + kMomChunk);
     const Real *base = frames + (f0 + fr) * orbits * (int64_t)n;
@@ -175,14 +179,15 @@ __global__ void merge_chunks(const Acc *part, int64_t items, int per_frame, int 
 }
 
 template <typename Real>
-cudaError_t launch_r_partial(const Real *frames, int64_t orbits, int n, int64_t f0, int C, int64_t blocks,
-                             Acc *part, cudaStream_t s) {
-    if (n <= 1) r_moments_partial<Real, 1><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, C, part);
-    else if (n <= 2) r_moments_partial<Real, 2><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, C, part);
-    else if (n <= 4) r_moments_partial<Real, 4><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, C, part);
-    else if (n <= 8) r_moments_partial<Real, 8><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, C, part);
-    else if (n <= 16) r_moments_partial<Real, 16><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, C, part);
-    else r_moments_partial<Real, 32><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, C, part);
+cudaError_t launch_r_partial(const Real *frames, int64_t orbits, int n, int64_t f0, int64_t nframes, int C,
+                             int64_t blocks, Acc *part, cudaStream_t s) {
+    unsigned long long *ck = check_word();
+    if (n <= 1) r_moments_partial<Real, 1><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, nframes, C, part, ck);
+    else if (n <= 2) r_moments_partial<Real, 2><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, nframes, C, part, ck);
+    else if (n <= 4) r_moments_partial<Real, 4><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, nframes, C, part, ck);
+    else if (n <= 8) r_moments_partial<Real, 8><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, nframes, C, part, ck);
+    else if (n <= 16) r_moments_partial<Real, 16><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, nframes, C, part, ck);
+    else r_moments_partial<Real, 32><<<(unsigned)blocks, kMomBlock, 0, s>>>(frames, orbits, n, f0, nframes, C, part, ck);
     return cudaGetLastError();
 }
 
@@ -207,8 +212,9 @@ FrameMomentsPlan frame_moments_plan(int64_t orbits, int n, int64_t count) {
 }
 
 cudaError_t launch_frame_moments_pass(const void *frames, bool fp64, int64_t orbits, int n, int64_t f0,
-                                      int64_t count, const FrameMomentsPlan &plan, void *partial,
+                                      int64_t count, int64_t nframes, const FrameMomentsPlan &plan, void *partial,
                                       double *state_out, double *r_out, cudaStream_t s) {
+    unsigned long long *ck = check_word();
     if (count <= 0) return cudaSuccess;
     const int C = plan.chunks;
     const int64_t blocks = (int64_t)C * count;
@@ -218,10 +224,10 @@ cudaError_t launch_frame_moments_pass(const void *frames, bool fp64, int64_t orb
     if (state_out != nullptr) {
         if (fp64)
             state_moments_partial<double><<<(unsigned)blocks, kMomBlock, 0, s>>>(
-                static_cast<const double *>(frames), orbits, n, f0, C, part_state);
+                static_cast<const double *>(frames), orbits, n, f0, nframes, C, part_state, ck);
         else
             state_moments_partial<float><<<(unsigned)blocks, kMomBlock, 0, s>>>(
-                static_cast<const float *>(frames), orbits, n, f0, C, part_state);
+                static_cast<const float *>(frames), orbits, n, f0, nframes, C, part_state, ck);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         merge_chunks<<<merge_grid(count * n), 256, 0, s>>>(part_state, count * n, n, C, state_out);
@@ -229,8 +235,10 @@ cudaError_t launch_frame_moments_pass(const void *frames, bool fp64, int64_t orb
         if (e != cudaSuccess) return e;
     }
     if (r_out != nullptr) {
-        e = fp64 ? launch_r_partial<double>(static_cast<const double *>(frames), orbits, n, f0, C, blocks, part_r, s)
-                 : launch_r_partial<float>(static_cast<const float *>(frames), orbits, n, f0, C, blocks, part_r, s);
+        e = fp64 ? launch_r_partial<double>(static_cast<const double *>(frames), orbits, n, f0, nframes, C, blocks,
+                                            part_r, s)
+                 : launch_r_partial<float>(static_cast<const float *>(frames), orbits, n, f0, nframes, C, blocks,
+                                           part_r, s);
         if (e != cudaSuccess) return e;
         merge_chunks<<<merge_grid(count), 256, 0, s>>>(part_r, count, 1, C, r_out);
         e = cudaGetLastError();

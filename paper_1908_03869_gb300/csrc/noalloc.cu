@@ -208,6 +208,8 @@ extern "C" sdeb_status sdeb_integrate_noalloc(const sdeb_problem *pb, const void
     a.dt = pb->dt;
     a.flags = flags;
     a.keys = philox_key_schedule(pb->seed);
+    a.nckpt = 0;
+    a.check = check_word();
     a.milstein = (pb->flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     a.rk4 = (pb->flags & SDEB_FLAG_RK4) ? 1 : 0;
     a.implicit = implicit_kind(pb->flags);

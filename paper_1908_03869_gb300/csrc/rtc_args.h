@@ -16,6 +16,8 @@ struct UserArgs {
     unsigned int k_begin, k_end, stride, orbit_offset;
     unsigned char *flags; // [orbits], bit 0 = non-finite
     PhiloxKeys keys;
+    long long nframes;    // frames in frames
+    unsigned long long *check;  // bounds-check status word (checked build), or null
 };
 
 }  // namespace sdeb

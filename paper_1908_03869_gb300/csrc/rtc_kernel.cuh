@@ -91,7 +91,8 @@ extern "C" __global__ void sdeb_user_kernel(const UserArgs a) {
             rtc_accumulate(x[i], c[i], f[i] * dt + noise);
         }
 #endif
-        if (frames != nullptr && (k + 1) % a.stride == 0) {
+        if (frames != nullptr && (k + 1) % a.stride == 0 &&
+            SDEB_CHECK(a.check, (long long)((k + 1) / a.stride) < a.nframes, kChkUserFrame, (k + 1) / a.stride)) {
             sdeb_real *fr = frames + ((long long)((k + 1) / a.stride) * a.orbits + o) * SDEB_N;
 #pragma unroll
             for (int i = 0; i < SDEB_N; ++i) fr[i] = x[i];

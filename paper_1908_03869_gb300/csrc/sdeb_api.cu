@@ -442,6 +442,12 @@ BatchArgs batch_args(const sdeb_ctx *c, void *x, float *comp, void *frames, uint
     a.frames = frames;
     a.flags = flags;
     a.keys = philox_key_schedule(c->pb.seed);
+    a.ninst = (int32_t)c->inst.size();
+    a.nitems = c->batch_items;
+    a.state_elems = c->batch_state_elems;
+    a.frame_elems = c->batch_frame_elems;
+    a.param_elems = c->batch_params_bytes / (int64_t)c->elem;
+    a.check = check_word();
     return a;
 }
 
@@ -618,6 +624,7 @@ const char *sdeb_status_string(sdeb_status s) {
     case SDEB_ESTATE: return "call order violated";
     case SDEB_EUNSUPPORTED: return "unsupported";
     case SDEB_ENONFINITE: return "non-finite state";
+    case SDEB_EBOUNDS: return "bounds check failed";
     default: return "unknown status";
     }
 }
@@ -854,6 +861,8 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
         u.orbit_offset = (uint32_t)ctx->pb.orbit_offset;
         u.flags = ctx->d_flags;
         u.keys = philox_key_schedule(ctx->pb.seed);
+        u.nframes = ctx->nframes;
+        u.check = check_word();
         cudaError_t e = rtc_launch(ctx->rtc, u, as_stream(stream));
         if (e != cudaSuccess) return cuda_fail(ctx, e, "user model kernel launch");
         ctx->k_current = k_end;
@@ -880,6 +889,8 @@ sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, 
     a.dt = ctx->pb.dt;
     a.flags = ctx->d_flags;
     a.keys = philox_key_schedule(ctx->pb.seed);
+    a.nckpt = ctx->nckpt;
+    a.check = check_word();
     a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
     a.rk4 = (ctx->pb.flags & SDEB_FLAG_RK4) ? 1 : 0;
     a.implicit = implicit_kind(ctx->pb.flags);
@@ -1005,7 +1016,8 @@ sdeb_status sdeb_frame_moments(sdeb_ctx *ctx, int64_t frame_begin, int64_t frame
         const int64_t cnt = std::min<int64_t>(plan.frames_per_pass, frame_count - f);
         double *st = mom ? (to_host ? stage : mom + f * n * 2) : nullptr;
         double *rt = rmom ? (to_host ? stage + cnt * n * 2 : rmom + f * 2) : nullptr;
-        e = launch_frame_moments_pass(ctx->d_frames, fp64, ctx->pb.orbits, n, frame_begin + f, cnt, plan, scratch,
+        e = launch_frame_moments_pass(ctx->d_frames, fp64, ctx->pb.orbits, n, frame_begin + f, cnt, ctx->nframes, plan,
+                                      scratch,
                                       st, rt, s);
         if (e == cudaSuccess && to_host && mom)
             e = cudaMemcpyAsync(mom + f * n * 2, st, (size_t)cnt * n * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1115,6 +1127,8 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
         a.dt = ctx->pb.dt;
         a.flags = tf;
         a.keys = philox_key_schedule(ctx->pb.seed);
+        a.nckpt = ctx->nckpt;
+        a.check = check_word();
         a.milstein = (ctx->pb.flags & SDEB_FLAG_MILSTEIN) ? 1 : 0;
         a.rk4 = (ctx->pb.flags & SDEB_FLAG_RK4) ? 1 : 0;
         a.implicit = implicit_kind(ctx->pb.flags);
@@ -1148,6 +1162,8 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
             g.dL_dxK = t_dl;
             g.dL_dp = t_dp;
             g.keys = a.keys;
+            g.nckpt = ctx->nckpt;
+            g.check = a.check;
             float ms_adj = 0.0f;
             // checkpoints 1 .. of the trial: copies of checkpoint 0
             const int64_t ck_used = (adj_steps + ctx->ckpt_int - 1) / ctx->ckpt_int;
@@ -1247,6 +1263,8 @@ sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_d
     a.dL_dp = shared ? ctx->d_gradp : dL_dp;
     a.dL_dx0 = dL_dx0;
     a.keys = philox_key_schedule(ctx->pb.seed);
+    a.nckpt = ctx->nckpt;
+    a.check = check_word();
     const bool fp64 = ctx->pb.precision == SDEB_FP64;
     const cudaStream_t s = as_stream(stream);
     cudaError_t e = launch_adjoint(a, ctx->layout, fp64, s);

@@ -63,6 +63,8 @@ std::string assemble(const sdeb_problem &pb, const char *user_source) {
                   pb.precision == SDEB_FP64 ? "double" : "float", pb.n, pb.m, pb.d,
                   (pb.flags & SDEB_FLAG_RK4) ? 1 : 0);
     std::string src = prelude;
+    src += kRtcCheck;
+    src += "\n";
     src += kRtcEmDevice;
     src += "\n";
     src += kRtcArgs;
@@ -103,7 +105,11 @@ sdeb_status rtc_build(const sdeb_problem &pb, const char *user_source, RtcModule
         log = "nvrtcCreateProgram failed";
         return SDEB_EINVAL;
     }
+#ifdef SDEB_CHECKED
+    const char *opts[] = {arch, "-std=c++17", "-default-device", "-DSDEB_RTC=1", "-DSDEB_CHECKED=1"};
+#else
     const char *opts[] = {arch, "-std=c++17", "-default-device", "-DSDEB_RTC=1"};
+#endif
     const nvrtcResult rc = api.compile(prog, 4, opts);
     size_t ls = 0;
     api.log_size(prog, &ls);
