@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "em_internal.h"
 #include "sdeb_rtc.h"
 #include "sdeb.h"
@@ -83,6 +85,17 @@ sdeb_status cuda_fail(sdeb_ctx *ctx, cudaError_t e, const char *what) {
 }
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+// An NVTX range over a host call (integration, gradient, batch, moments,
+// tuning), so a timeline tool shows which library call enqueued which
+// kernels.  NVTX v3 is header-only: without an attached tool a range costs a
+// branch.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Host-side fault injection for failure-detection tests, nothing on the
 // device: SDEB_FAULT="alloc:<k>" makes the k-th allocation of a context's
@@ -452,6 +465,7 @@ BatchArgs batch_args(const sdeb_ctx *c, void *x, float *comp, void *frames, uint
 }
 
 sdeb_status integrate_batch(sdeb_ctx *c, cudaStream_t s) {
+    NvtxRange nvtx_range("sdeb_integrate (batch)");
     if (!c->params_set) return fail(c, SDEB_ESTATE, "sdeb_set_params has not been called");
     if (c->batch_done) return fail(c, SDEB_ESTATE, "batch already integrated; call sdeb_set_params to rerun");
     cudaError_t e = cudaSuccess;
@@ -836,6 +850,7 @@ sdeb_status sdeb_set_params(sdeb_ctx *ctx, const void *params, const void *x0, i
 }
 
 sdeb_status sdeb_integrate_range(sdeb_ctx *ctx, int64_t k_begin, int64_t k_end, void *stream) {
+    NvtxRange nvtx_range("sdeb_integrate_range");
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "a batch integrates whole horizons (sdeb_integrate)");
     if (!ctx->params_set) return fail(ctx, SDEB_ESTATE, "sdeb_set_params has not been called");
@@ -979,6 +994,7 @@ sdeb_status sdeb_read_final(sdeb_ctx *ctx, void *dst, size_t dst_bytes, int32_t 
 sdeb_status sdeb_frame_moments(sdeb_ctx *ctx, int64_t frame_begin, int64_t frame_count, double *mom,
                                size_t mom_bytes, double *rmom, size_t rmom_bytes, int32_t dst_on_device,
                                void *stream) {
+    NvtxRange nvtx_range("sdeb_frame_moments");
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "moments are per context, not per batch");
     if (!mom && !rmom) return fail(ctx, SDEB_EINVAL, "mom and rmom are both NULL");
@@ -1065,6 +1081,7 @@ sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int32_t unit
 }
 
 sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
+    NvtxRange nvtx_range("sdeb_autotune");
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (ctx->is_batch) return autotune_batch(ctx, as_stream(stream));
     if (!ctx->params_set || ctx->k_current != 0)
@@ -1232,6 +1249,7 @@ sdeb_status sdeb_frames_device_ptr(sdeb_ctx *ctx, void **ptr, size_t *bytes) {
 }
 
 sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_dx0, void *stream) {
+    NvtxRange nvtx_range("sdeb_grad");
     if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
     if (ctx->is_batch) return fail(ctx, SDEB_EUNSUPPORTED, "the adjoint is not available on batches");
     if (!dL_dxK || !dL_dp) return fail(ctx, SDEB_EINVAL, "dL_dxK and dL_dp must not be NULL");
