@@ -161,32 +161,38 @@ __device__ __forceinline__ void sincos_approx_f32(float x, float &s, float &c) {
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
-// FP32, in polar form: the pair is (amp c, amp s), amp = -radius.
-// y = -2 ln U1 comes from the SFU log2 except when U1 is within 2^-6 of 1,
-// where the absolute error of an SFU logarithm would dominate: there
-// t = 1 - U1 = (~w + 1/2) 2^-32 comes from the complement word and
-// -2 ln(1 - t) = t (2 + t + 2t^2/3 + t^3/2) + O(t^5), the dropped terms
-// (2t^5/5 + ...) below t^4/5 <= 2^-24/5 relative for t <= 2^-6.  The angle
-// is 2 pi (U2 - 1/2) from the centred word in one rounding, an argument in
+// FP32, in polar form, with the amplitude in units of sqrt(2 ln 2): the pair
+// is (a c, a s) with a = kBmAmpUnitF32 * amp, amp = -sqrt(y'),
+// y' = -2 ln(U1) / (2 ln 2) = -log2 U1.  Leaving the constant factor to the
+// caller (which folds it into the noise strength) saves a multiply per pair.
+// y' comes from the SFU log2 except when U1 is within 2^-6 of 1, where the
+// absolute error of an SFU logarithm would dominate: there t = 1 - U1 =
+// (~w + 1/2) 2^-32 comes from the complement word and
+// -log2(1 - t) = t (2 + t + 2t^2/3 + t^3/2) / (2 ln 2) + O(t^5), the dropped
+// terms below t^4/5 <= 2^-24/5 relative for t <= 2^-6 (the coefficients are
+// pre-divided by 2 ln 2).  The angle is 2 pi (U2 - 1/2) = 2 pi w 2^-32 - pi
+// (1 - 2^-32) in one fused multiply-add of the converted word, an argument in
 // [-pi, pi] for the SFU: cos(2 pi U2) = -cos(2 pi (U2 - 1/2)), likewise for
 // sin, hence the negative amplitude.
+constexpr float kBmAmpUnitF32 = 1.17741002251547469f;  // sqrt(2 ln 2)
+
 __device__ __forceinline__ void box_muller_polar_f32(uint32_t w_first, uint32_t w_second, float &amp, float &c,
                                                      float &s) {
-    const float kMinus2Ln2 = -1.38629436111989061883f;  // -2 ln 2
     // For w >= 2^31 the signed reading of w is w - 2^32 = -(comp + 1), comp =
     // 2^32 - 1 - w the complement word, so t = 1 - U1 = (comp + 1/2) 2^-32 is
     // one fma of it; t is only used when comp < 2^26.
     const float t = __fmaf_rn(__int2float_rn((int32_t)w_first), -0x1p-32f, -0x1p-33f);
-    float poly = __fmaf_rn(t, 0.5f, 2.0f / 3.0f);
-    poly = __fmaf_rn(poly, t, 1.0f);
-    poly = __fmaf_rn(poly, t, 2.0f);
+    float poly = __fmaf_rn(t, 0.360673760222240845f, 0.480898346962987793f);  // 1/(4 ln 2), 1/(3 ln 2)
+    poly = __fmaf_rn(poly, t, 0.721347520444481703f);                         // 1/(2 ln 2)
+    poly = __fmaf_rn(poly, t, 1.44269504088896341f);                          // 1/ln 2
     const float y_series = t * poly;
-    const float y_log = kMinus2Ln2 * lg2_approx_f32(uniform_f32(w_first));
+    const float y_log = -lg2_approx_f32(uniform_f32(w_first));
     const float y = (w_first > 0xFBFFFFFFu) ? y_series : y_log;  // comp < 2^26
     amp = -sqrt_approx_f32(y);
-    // float(2 pi) 2^-32 and float(2 pi) 2^-33: exact scalings of float(2 pi)
-    const float ang = __fmaf_rn(__int2float_rn((int32_t)(w_second ^ 0x80000000u)), 0x1.921fb6p-30f,
-                                0x1.921fb6p-31f);
+    // 2 pi 2^-32 (an exact scaling of float(2 pi)) and -float(pi): the word's
+    // conversion rounds at most 2^8, the constant 8.7e-8 and the sum once,
+    // below 6e-7 rad in all
+    const float ang = __fmaf_rn(__uint2float_rn(w_second), 0x1.921fb6p-30f, -0x1.921fb6p+1f);
     sincos_approx_f32(ang, s, c);
 }
 
@@ -194,8 +200,9 @@ __device__ __forceinline__ void box_muller_f32(uint32_t w_first, uint32_t w_seco
                                                float &n_sin) {
     float amp, c, s;
     box_muller_polar_f32(w_first, w_second, amp, c, s);
-    n_cos = amp * c;
-    n_sin = amp * s;
+    const float a = amp * kBmAmpUnitF32;
+    n_cos = a * c;
+    n_sin = a * s;
 }
 
 // FP64, polar form: amp = radius, (c, s) = (cos, sin)(2 pi U2).
@@ -214,6 +221,11 @@ __device__ __forceinline__ void box_muller_f64(uint32_t w_first, uint32_t w_seco
     n_cos = amp * c;
     n_sin = amp * s;
 }
+
+// The factor box_muller_polar leaves out of the amplitude (FP32: sqrt(2 ln 2);
+// FP64: 1, the amplitude is the radius).
+template <typename Real>
+__device__ __forceinline__ constexpr Real bm_amp_unit() { return sizeof(Real) == 4 ? Real(kBmAmpUnitF32) : Real(1); }
 
 template <typename Real>
 __device__ __forceinline__ void box_muller_polar(uint32_t w_first, uint32_t w_second, Real &amp, Real &c, Real &s);

@@ -193,7 +193,7 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
     if constexpr (M::kSplitNoise) {
         Real amp_s[kNoisePairs<P>];
 #pragma unroll
-        for (int j = 0; j < kNoisePairs<P>; ++j) amp_s[j] = model.noise_scaled(amp[j]);
+        for (int j = 0; j < kNoisePairs<P>; ++j) amp_s[j] = model.noise_scaled(amp[j]);  // includes bm_amp_unit
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             Real inc[M::U];
@@ -203,9 +203,11 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
                 if constexpr (M::kDelayedComp) accumulate_delayed(x[c][i], cp[c][i], inc[c]);
                 else accumulate(x[c][i], cp[c][i], inc[c]);
             }
-            if constexpr (RECORD) rec->z[i] = mul_r(amp[noise_pair<P>(i)], trig[i]);
+            if constexpr (RECORD) rec->z[i] = mul_r(mul_r(amp[noise_pair<P>(i)], bm_amp_unit<Real>()), trig[i]);
         }
     } else {
+#pragma unroll
+        for (int j = 0; j < kNoisePairs<P>; ++j) amp[j] = mul_r(amp[j], bm_amp_unit<Real>());
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const Real z = mul_r(amp[noise_pair<P>(i)], trig[i]);

@@ -46,6 +46,7 @@ struct KuramotoLane {
     Real omega_dt[P];         // omega_i dt
     Real live[P];             // 1 for the orbit's units, 0 for padding
     Real gsq[PAPER ? P : 1];  // noise strength times sqrt(dt)
+    Real gsq_bm;              // g sqrt(dt) times the factor box_muller_polar leaves out
     Real kn;                  // K / n
     Real kn_dt;               // (K / n) dt
     Real sn[P], cs[P];
@@ -53,7 +54,10 @@ struct KuramotoLane {
     __device__ __forceinline__ void load(const Real *p, int u0, int units, Real dt, Real sqdt) {
         kn = p[0] / (Real)units;
         kn_dt = mul_r(kn, dt);
-        if (!PAPER) gsq[0] = p[1] * sqdt;
+        if (!PAPER) {
+            gsq[0] = p[1] * sqdt;
+            gsq_bm = mul_r(gsq[0], bm_amp_unit<Real>());
+        }
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             int j = u0 + i;
@@ -119,9 +123,10 @@ struct KuramotoLane {
         inc[0] = fma_r(kS, cs[i], fma_r(-kC, sn[i], fma_r(gsq[PAPER ? i : 0], N, omega_dt[i])));
     }
 
-    // The scalar noise strength g sqrt(dt) times a Box-Muller amplitude, once
-    // per pair; the increment is then f dt + (g sqrt(dt) amp) trig.
-    __device__ __forceinline__ Real noise_scaled(Real amp) const { return mul_r(gsq[0], amp); }
+    // The scalar noise strength g sqrt(dt) times a Box-Muller amplitude (and
+    // the factor the polar form leaves out), once per pair; the increment is
+    // then f dt + (g sqrt(dt) amp) trig.
+    __device__ __forceinline__ Real noise_scaled(Real amp) const { return mul_r(gsq_bm, amp); }
 
     __device__ __forceinline__ void incr_split(int i, const Real (&red)[NR], Real amp_scaled, Real trig,
                                                Real (&inc)[U]) const {
