@@ -29,9 +29,10 @@ __device__ __forceinline__ void flag_nonfinite(uint8_t *flag, const Real (&x)[1]
 // item's lane group, the group sums with `reduce`.  Steps 0..kmax-1 are taken
 // (the group's shuffles or barriers need every lane), the item's own state is
 // stored, framed and flagged only while k < its step count (`live`).
-template <typename Real, int P, class RED>
+template <typename Real, int P, class RED, bool SHARE_PHILOX = false>
 __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it, bool has, int lane, uint32_t kmax,
                                          RED &reduce) {
+    static_assert(!SHARE_PHILOX || P == 2, "Philox sharing pairs lanes of two units");
     using M = KuramotoLane<Real, P, false>;
     constexpr bool kKahan = std::is_same<Real, float>::value;
     const BatchInstance in = a.inst[it.instance];
@@ -75,11 +76,36 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
         if (live) mine = min(mine, min(to_frame, steps - k));
         const uint32_t run = __reduce_min_sync(0xffffffffu, mine);
 #pragma unroll 1
-        for (uint32_t s = 0; s < run; ++s) {
+        for (uint32_t s = 0; s < run;) {
+            if constexpr (SHARE_PHILOX) {
+                // Lanes 2b and 2b + 1 (units 4b.. and 4b + 2..) use the two
+                // halves of noise block b: over a pair of steps each lane
+                // draws the block for one of the steps (the even lane step
+                // k, the odd lane step k + 1) and hands its partner the half
+                // the partner uses, so a block costs one Philox call per
+                // step instead of two.
+                if (s + 2 <= run) {
+                    const bool odd = (lane & 1) != 0;
+                    const U32x4 w = philox4x32_10_fixed(k + s + (odd ? 1u : 0u), noise.r1[0], a.keys);
+                    const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? w.x : w.z, 1);
+                    const uint32_t r1 = __shfl_xor_sync(0xffffffffu, odd ? w.y : w.w, 1);
+                    em_step_words<M, Real>(model, x, cp, odd ? r0 : w.x, odd ? r1 : w.y, u0, units, reduce);
+                    if constexpr (M::kDelayedComp) {
+                        if (((k + s + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
+                    }
+                    em_step_words<M, Real>(model, x, cp, odd ? w.z : r0, odd ? w.w : r1, u0, units, reduce);
+                    if constexpr (M::kDelayedComp) {
+                        if (((k + s + 2u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
+                    }
+                    s += 2;
+                    continue;
+                }
+            }
             em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
             if constexpr (M::kDelayedComp) {
                 if (((k + s + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
             }
+            ++s;
         }
         k += run;
         if (live) {
@@ -194,6 +220,43 @@ struct NamedTeamSum {
     }
 };
 
+// FP32: the team's sums in 32-bit fixed point, multiples of 2^-22 (a sum
+// over at most 256 units of terms in [-1, 1] stays below 2^30): each lane's
+// partial rounded once, added across the warp by one redux.sync and across
+// the team's warps through shared memory.  Integer addition is exact, so the
+// totals are the same bits in every lane and in any order, and the rounding
+// (at most 2^-23 per lane) is of the order of the FP32 butterfly's.
+template <int NW, int BAR>
+struct NamedTeamSum<NW, BAR, float> {
+    float *buf;  // [2][NW][2] words in shared memory, used as int
+    int flip;
+    int warp0;
+    template <int NR>
+    __device__ __forceinline__ void operator()(float (&r)[NR]) {
+        static_assert(NR <= 2, "two sums at most");
+        const int warp = (threadIdx.x >> 5) - warp0, lane = threadIdx.x & 31;
+        int *slot = reinterpret_cast<int *>(buf) + flip * NW * 2;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int ws = __reduce_add_sync(0xffffffffu, __float2int_rn(r[q] * 0x1p22f));
+            if (lane == 0) slot[warp * 2 + q] = ws;
+        }
+        if constexpr (BAR == 0) {
+            __syncthreads();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NW * 32) : "memory");
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            int t = slot[q];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) t += slot[w * 2 + q];
+            r[q] = __int2float_rn(t) * 0x1p-22f;
+        }
+        flip ^= 1;
+    }
+};
+
 template <typename Real, int NW, int P, int BAR>
 __device__ __forceinline__ void run_team(const BatchArgs &a, int32_t item, Real *buf, int warp0) {
     NamedTeamSum<NW, BAR, Real> reduce{buf, 0, warp0};
@@ -202,7 +265,8 @@ __device__ __forceinline__ void run_team(const BatchArgs &a, int32_t item, Real 
     const BatchItem it = a.items[item];
     if (!SDEB_CHECK(a.check, it.instance >= 0 && it.instance < a.ninst, kChkBatchInstance, it.instance)) return;
     const uint32_t steps = a.inst[it.instance].steps;
-    run_item<Real, P>(a, it, true, (int)threadIdx.x - warp0 * 32, steps, reduce);
+    run_item<Real, P, NamedTeamSum<NW, BAR, Real>, P == 2>(a, it, true, (int)threadIdx.x - warp0 * 32, steps,
+                                                           reduce);
 }
 
 // Registers capped for five resident blocks per SM (96 per thread, a few

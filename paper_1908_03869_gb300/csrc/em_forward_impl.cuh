@@ -166,20 +166,11 @@ struct StepRecord {
     Real sums[2];
 };
 
+// The step of Eq. 2 given its normals in polar form (em_step draws them).
 template <class M, typename Real, int P, bool RECORD = false, class RED>
-__device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], uint32_t k,
-                                        const NoiseLane<P> &nl, int u0, int units, const PhiloxKeys &keys,
-                                        RED &reduce, StepRecord<Real, P> *rec = nullptr) {
-    static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
-    Real amp[kNoisePairs<P>], trig[P];
-    if constexpr (M::kNoise) {
-        draw_noise<Real, P>(amp, trig, k, u0, nl, keys);
-    } else {
-#pragma unroll
-        for (int j = 0; j < kNoisePairs<P>; ++j) amp[j] = Real(0);
-#pragma unroll
-        for (int i = 0; i < P; ++i) trig[i] = Real(0);
-    }
+__device__ __forceinline__ void em_step_noise(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P],
+                                              Real (&amp)[kNoisePairs<P>], const Real (&trig)[P], int u0, int units,
+                                              RED &reduce, StepRecord<Real, P> *rec = nullptr) {
     constexpr int NRA = M::NR > 0 ? M::NR : 1;
     Real red[NRA];
     model.prepare(x, cp, u0, units, red);
@@ -221,6 +212,34 @@ __device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)
             if constexpr (RECORD) rec->z[i] = z;
         }
     }
+}
+
+template <class M, typename Real, int P, bool RECORD = false, class RED>
+__device__ __forceinline__ void em_step(M &model, Real (&x)[M::U][P], Real (&cp)[M::U][P], uint32_t k,
+                                        const NoiseLane<P> &nl, int u0, int units, const PhiloxKeys &keys,
+                                        RED &reduce, StepRecord<Real, P> *rec = nullptr) {
+    static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
+    Real amp[kNoisePairs<P>], trig[P];
+    if constexpr (M::kNoise) {
+        draw_noise<Real, P>(amp, trig, k, u0, nl, keys);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kNoisePairs<P>; ++j) amp[j] = Real(0);
+#pragma unroll
+        for (int i = 0; i < P; ++i) trig[i] = Real(0);
+    }
+    em_step_noise<M, Real, P, RECORD>(model, x, cp, amp, trig, u0, units, reduce, rec);
+}
+
+// The step for a lane of 2 units whose Philox word pair (wa, wb) is given
+// (a pair of lanes sharing a noise block can split the block's two Philox
+// calls of two steps between them).
+template <class M, typename Real, class RED>
+__device__ __forceinline__ void em_step_words(M &model, Real (&x)[M::U][2], Real (&cp)[M::U][2], uint32_t wa,
+                                              uint32_t wb, int u0, int units, RED &reduce) {
+    Real amp[1], trig[2];
+    box_muller_polar<Real>(wa, wb, amp[0], trig[0], trig[1]);
+    em_step_noise<M, Real, 2>(model, x, cp, amp, trig, u0, units, reduce);
 }
 
 // End of a compensation period (models with kDelayedComp): every unit's
