@@ -66,11 +66,9 @@ FALLBACK_SM_MHZ = 2070.0
 FORWARD_SOURCES = ["em_forward_impl.cuh", "em_device.cuh", "em_models.cuh", "fwd_kuramoto_f32.cu",
                    "fwd_kuramoto_f64.cu", "em_internal.h"]
 NCU_COUNTERS = {
-    # DRAM bytes (read + write) of one forward launch of the n = 32 problem
-    # (profiles/em_forward_kuramoto_fp32_n32_dram_full_size.md)
+    # DRAM bytes (read + write) of one full-size forward launch of the n = 32 problem
     "forward_n32_dram_bytes": {"sha": "7ab85ad11493d958", "value": 3.481e9},
-    # FP64-pipe thread-instructions per oscillator-step of the FP64 forward
-    # kernel (profiles/em_forward_kuramoto_fp64_n32_sections.md)
+    # FP64-pipe thread-instructions per oscillator-step of the FP64 forward kernel
     "fp64_pipe_inst_per_osc_step": {"sha": "7ab85ad11493d958", "value": 65.63},
 }
 
