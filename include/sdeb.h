@@ -97,10 +97,10 @@ enum {
 /* Precision.  FP32_KAHAN: float state with a Kahan compensation word per
  * state component, float arithmetic, FP64 time variable.  FP64: double
  * everywhere.  For the Kuramoto models under Euler-Maruyama (and Milstein)
- * the FP32 compensation is applied every 4 steps, at step multiples of 4:
- * in between, each increment enters the compensation word alone (one
- * rounding at the size of a few increments), and the drift reads the phase
- * x - c.  A state kept for resuming (after sdeb_integrate_range) is the
+ * the FP32 compensation is applied every 16 steps, at step multiples of
+ * 16: in between, each increment enters the compensation word alone (one
+ * rounding at the size of at most 16 increments), and the drift reads the
+ * phase x - c.  A state kept for resuming (after sdeb_integrate_range) is the
  * pair (x, c); frames, sdeb_read_final and the allocation-free path return
  * its value x - c. */
 enum { SDEB_FP32_KAHAN = 0, SDEB_FP64 = 1 };
@@ -359,6 +359,17 @@ SDEB_API sdeb_status sdeb_frame_moments(sdeb_ctx *ctx, int64_t frame_begin, int6
  * Supported models: SDEB_KURAMOTO, SDEB_KURAMOTO_PAPER (others: EUNSUPPORTED). */
 SDEB_API sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_dx0, void *stream);
 
+/* Where sdeb_grad's replay keeps a segment's step records (see
+ * sdeb_get_checkpoint_interval).  AUTO (the default): in shared memory when
+ * the segment's records take at most 112 KB per block of 128 threads at the
+ * context's layout, else in the global buffer.  GLOBAL: always the global
+ * buffer.  SHARED: shared memory, and sdeb_grad returns EUNSUPPORTED where
+ * they do not fit.  The two places give the same bits (the sweep takes the
+ * sine and cosine of the recorded phase with the replay's own function).
+ * EINVAL for another mode, a NULL or batch context. */
+enum { SDEB_RECORDS_AUTO = 0, SDEB_RECORDS_GLOBAL = 1, SDEB_RECORDS_SHARED = 2 };
+SDEB_API sdeb_status sdeb_set_adjoint_records(sdeb_ctx *ctx, int32_t mode);
+
 /* Per-orbit status bits after the last integration: bit 0 = a state
  * component is not finite.  dst: host [orbits]; synchronises `stream`. */
 SDEB_API sdeb_status sdeb_orbit_flags(sdeb_ctx *ctx, uint8_t *dst, void *stream);
@@ -381,16 +392,20 @@ SDEB_API sdeb_status sdeb_set_layout(sdeb_ctx *ctx, int32_t lanes_per_orbit, int
 
 /* The checkpoint interval a context keeps (0 without checkpoints, and for a
  * batch).  For sdeb_grad the adjoint replays each segment between two
- * checkpoints into a buffer of phases, normals and coupling sums (2 n + 2
- * values per orbit and step) that its reverse sweep reads back; when that
- * buffer, for all orbits resident on the GPU at once, would outgrow half the
- * L2 cache, sdeb_create keeps checkpoints more often than ckpt_every -- every
- * ceil(ckpt_every / m) steps, m <= 16, rounded down to a multiple of 4 above
- * 4 -- so the buffer stays on chip instead of making a round trip through
- * HBM.  Checkpoint memory is
- * (steps / interval + 1) x orbits x n elements (FP32: twice that, with the
- * compensation words).  Gradients do not depend on the interval beyond
- * rounding. */
+ * checkpoints and keeps a record of every step (each unit's sine, cosine or
+ * phase, and normal; the orbit's coupling sums C, S) that its reverse sweep
+ * reads back.  sdeb_create keeps checkpoints every 8 steps (when ckpt_every
+ * > 8) as long as they take at most a quarter of the device memory: a
+ * segment's records then fit the shared memory of the thread that writes
+ * and reads them, and no record leaves the SM.  Otherwise the records go
+ * through a global buffer (2 n + 2 values per orbit and step), and when
+ * that buffer, for all orbits resident on the GPU at once, would outgrow
+ * 60 % of the L2 cache the interval is ceil(ckpt_every / m), m <= 16,
+ * rounded down to a multiple of the FP32 compensation period above it, so
+ * the buffer stays on chip instead of making a round trip through HBM.
+ * Checkpoint memory is (steps / interval + 1) x orbits x n elements (FP32:
+ * twice that, with the compensation words).  Gradients do not depend on the
+ * interval beyond rounding. */
 SDEB_API sdeb_status sdeb_get_checkpoint_interval(const sdeb_ctx *ctx, int64_t *steps);
 SDEB_API sdeb_status sdeb_get_layout(const sdeb_ctx *ctx, int32_t *lanes_per_orbit, int32_t *units_per_lane);
 

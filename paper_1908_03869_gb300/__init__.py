@@ -25,7 +25,8 @@ __all__ = [
     "sdeb_create", "sdeb_destroy", "sdeb_set_params", "sdeb_integrate", "sdeb_integrate_range",
     "sdeb_read_orbits", "sdeb_read_final", "sdeb_frame_moments", "sdeb_grad", "sdeb_orbit_flags", "sdeb_frames_device_ptr",
     "sdeb_last_error", "sdeb_status_string", "sdeb_philox_fill", "sdeb_normals_fill", "sdeb_order_param",
-    "sdeb_integrate_noalloc", "sdeb_pipe_rate", "sdeb_set_layout", "sdeb_get_layout", "sdeb_get_checkpoint_interval", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
+    "sdeb_integrate_noalloc", "sdeb_pipe_rate", "sdeb_set_layout", "sdeb_get_layout", "sdeb_get_checkpoint_interval",
+    "sdeb_set_adjoint_records", "SDEB_RECORDS_AUTO", "SDEB_RECORDS_GLOBAL", "SDEB_RECORDS_SHARED", "sdeb_autotune", "sdeb_create_batch", "sdeb_batch_read",
     "sdeb_batch_info", "sdeb_batch_layout", "sdeb_batch_set_schedule", "sdeb_batch_plan", "model_shape",
     "sdeb_swarm_expand", "sdeb_swarm_fitness", "sdeb_swarm_update", "SDEB_SWARM_MAX_DIMS", "PIPES",
     "SDEB_MEM_HOST", "SDEB_MEM_DEVICE", "SDEB_MEM_HOST_ASYNC",
@@ -41,6 +42,7 @@ SDEB_FLAG_SHARED_PARAMS, SDEB_FLAG_NO_FRAMES, SDEB_FLAG_MILSTEIN, SDEB_FLAG_RK4 
 SDEB_FLAG_IMPLICIT_EULER, SDEB_FLAG_IMPLICIT_MIDPOINT = 16, 32
 SDEB_SWARM_MAX_DIMS = 16
 SDEB_MEM_HOST, SDEB_MEM_DEVICE, SDEB_MEM_HOST_ASYNC = 0, 1, 2
+SDEB_RECORDS_AUTO, SDEB_RECORDS_GLOBAL, SDEB_RECORDS_SHARED = 0, 1, 2
 IMPLICIT_FLAGS = {None: 0, "euler": SDEB_FLAG_IMPLICIT_EULER, "midpoint": SDEB_FLAG_IMPLICIT_MIDPOINT}
 
 MODEL_IDS = {
@@ -126,6 +128,7 @@ _SIGS = {
     "sdeb_set_layout": (_ST, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sdeb_get_layout": (_ST, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "sdeb_get_checkpoint_interval": (_ST, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "sdeb_set_adjoint_records": (_ST, [_P, ctypes.c_int32]),
     "sdeb_autotune": (_ST, [_P, ctypes.c_int64, _P]),
     "sdeb_create_batch": (_ST, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "sdeb_create_user": (_ST, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
@@ -301,6 +304,10 @@ def sdeb_get_layout(ctx):
     g, p = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().sdeb_get_layout(ctx, ctypes.byref(g), ctypes.byref(p)), ctx)
     return g.value, p.value
+
+
+def sdeb_set_adjoint_records(ctx, mode):
+    _check(lib().sdeb_set_adjoint_records(ctx, mode), ctx)
 
 
 def sdeb_get_checkpoint_interval(ctx):

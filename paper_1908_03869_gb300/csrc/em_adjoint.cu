@@ -11,7 +11,7 @@
 // with A = sum_i lambda^{k+1}_i cos x_i, B = sum_i lambda^{k+1}_i sin x_i,
 // C = sum_j cos x_j, S = sum_j sin x_j at x = theta^k (the pairwise sums
 // sum_i lambda_i cos(x_i - x_l) and sum_j cos(x_j - x_l) rewritten exactly);
-//   dL/dK      += (dt / n) sum_i lambda^{k+1}_i (S cos x_i - C sin x_i),
+//   dL/dK      += (dt / n) sum_i lambda^{k+1}_i (S cos x_i - C sin x_i) = (dt / n) (S A - C B),
 //   dL/domega_i += dt lambda^{k+1}_i,
 //   dL/dg      += sqrt(dt) sum_i lambda^{k+1}_i N^k_i   (g = sigma, or p_i per unit),
 // and dL/dtheta^0 = lambda^0.
@@ -19,11 +19,12 @@
 // States are recomputed segment by segment from the checkpoints the forward
 // pass stored every ckpt_every steps, with the same step code (bit-identical
 // trajectory).  The forward pass stores no noise: the replay regenerates the
-// Philox normals of each step (they drive the recomputed states), and keeps
-// them, with the step's reduced phase (FP32: x - c folded into [-pi, pi])
-// and the orbit's coupling sums C and S, in a segment buffer that the
-// reverse sweep of the same segment reads back (the sweep takes sin and cos
-// of the phase again, but not C and S).
+// Philox normals of each step (they drive the recomputed states) and keeps
+// them, with the sine and cosine of each unit's phase and the orbit's
+// coupling sums C and S, for the reverse sweep of the same segment: in the
+// shared memory of the thread (segments short enough to fit), or in a global
+// segment buffer with the reduced phase (FP32: x - c folded into [-pi, pi])
+// in place of sine and cosine, which the sweep then takes again.
 #include <type_traits>
 
 #include "em_forward_impl.cuh"
@@ -32,10 +33,56 @@ namespace sdeb {
 
 namespace {
 
-template <bool PAPER, typename Real, int G, int P>
+// Step step_off's record of orbit o from the global segment buffer.
+template <typename Real, int P>
+__device__ __forceinline__ void load_record(const Real *seg, const Real *seg_sums, uint32_t step_off, int64_t orbits,
+                                            int64_t o, int64_t n, int units, int u0, Real (&r)[1][P],
+                                            Real (&z)[1][P], Real &C, Real &S) {
+    const int64_t rowi = (int64_t)step_off * orbits + o;
+    const Real *row = seg + rowi * (2 * n);
+    load_units<Real, 1, P>(row, units, u0, r);
+    load_units<Real, 1, P>(row + n, units, u0, z);
+    C = seg_sums[2 * rowi];
+    S = seg_sums[2 * rowi + 1];
+}
+
+// A vector of V Reals, aligned to its size (one 8- or 16-byte shared-memory
+// access).
+template <typename Real, int V>
+struct alignas(V * sizeof(Real)) RVec {
+    Real v[V];
+};
+
+// The records a thread keeps per step when the segment's records sit in
+// shared memory: sine, cosine and normal of each unit in vectors of V Reals
+// (V = P up to 16 bytes), and the orbit's C, S as one pair.
+template <typename Real, int P>
+struct SmemRec {
+    static constexpr int V = P * (int)sizeof(Real) < 16 ? P : 16 / (int)sizeof(Real);
+    static constexpr int NV = 3 * P / V;  // vectors per step: sines, cosines, normals
+    using Vec = RVec<Real, V>;
+    using Pair = RVec<Real, 2>;
+    static constexpr int64_t kStepBytes = (int64_t)NV * sizeof(Vec) + (int64_t)sizeof(Pair);
+};
+
+// SMEM: the replay keeps the segment's records in shared memory (dynamic:
+// ckpt_every steps x SmemRec::kStepBytes per thread).  The vectors of step s
+// come first, vector v of thread t at index (s * NV + v) * blockDim + t, then
+// the pairs, step s of thread t at s * blockDim + t: consecutive threads
+// access consecutive addresses.  The sweep reads back the sine and cosine
+// the replay's drift took instead of taking them again.  Otherwise the
+// records go through the global segment buffer.
+template <bool PAPER, typename Real, int G, int P, bool SMEM>
 __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const AdjointArgs a) {
     using M = KuramotoLane<Real, P, PAPER>;
     static_assert(P == 1 || P == 2 || P % 4 == 0, "a lane holds 1, 2 or a multiple of 4 units");
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    using SR = SmemRec<Real, P>;
+    constexpr int V = SR::V, NV = SR::NV;
+    typename SR::Vec *const vrec = reinterpret_cast<typename SR::Vec *>(adj_smem) + threadIdx.x;
+    typename SR::Pair *const prec =
+        reinterpret_cast<typename SR::Pair *>(adj_smem + (size_t)a.ckpt_every * NV * kForwardBlock *
+                                                             sizeof(typename SR::Vec)) + threadIdx.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t orbit = tid / G;
     const int lig = (int)(tid & (G - 1));
@@ -101,7 +148,25 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             if constexpr (M::kDelayedComp) {
                 if (((k + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
             }
-            if (active && SDEB_CHECK(a.check, k - k0 < a.ckpt_every, kChkAdjointSeg, k - k0)) {
+            if constexpr (SMEM) {
+                if (SDEB_CHECK(a.check, k - k0 < a.ckpt_every, kChkAdjointSeg, k - k0)) {
+                    typename SR::Vec *row = vrec + (int)(k - k0) * NV * kForwardBlock;
+#pragma unroll
+                    for (int v = 0; v < P / V; ++v) {
+                        typename SR::Vec vs, vc, vz;
+#pragma unroll
+                        for (int j = 0; j < V; ++j) {
+                            vs.v[j] = model.sn[v * V + j];
+                            vc.v[j] = model.cs[v * V + j];
+                            vz.v[j] = rec.z[v * V + j];
+                        }
+                        row[v * kForwardBlock] = vs;
+                        row[(P / V + v) * kForwardBlock] = vc;
+                        row[(2 * P / V + v) * kForwardBlock] = vz;
+                    }
+                    prec[(int)(k - k0) * kForwardBlock] = typename SR::Pair{{rec.sums[0], rec.sums[1]}};
+                }
+            } else if (active && SDEB_CHECK(a.check, k - k0 < a.ckpt_every, kChkAdjointSeg, k - k0)) {
                 const int64_t rowi = (int64_t)(k - k0) * a.orbits + o;
                 Real *row = seg + rowi * (2 * n);
                 store_units<Real, 1, P>(row, units, u0, *reinterpret_cast<const Real(*)[1][P]>(&rec.phase));
@@ -113,63 +178,70 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
             }
         }
         // ---- reverse sweep ---------------------------------------------------
-        // the next row (step k - 1) is loaded while step k is processed
-        Real rn[1][P], zn[1][P], Cn, Sn;
+        // (global records: the next row, step k - 1, is loaded while step k
+        // is processed)
+        Real rn[1][P], zn[1][P], Cn = Real(0), Sn = Real(0);
         (void)SDEB_CHECK(a.check, k1 > k0 && k1 - 1 - k0 < a.ckpt_every, kChkAdjointSeg, k1 - k0);
-        {
-            const int64_t rowi = (int64_t)(k1 - 1 - k0) * a.orbits + o;
-            const Real *row = seg + rowi * (2 * n);
-            load_units<Real, 1, P>(row, units, u0, rn);
-            load_units<Real, 1, P>(row + n, units, u0, zn);
-            Cn = seg_sums[2 * rowi];
-            Sn = seg_sums[2 * rowi + 1];
-        }
+        if constexpr (!SMEM) load_record(seg, seg_sums, k1 - 1 - k0, a.orbits, o, n, units, u0, rn, zn, Cn, Sn);
         for (uint32_t kk = k1; kk > k0; --kk) {
             const uint32_t k = kk - 1;
-            Real r[1][P], z[1][P];
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-                r[0][i] = rn[0][i];
-                z[0][i] = zn[0][i];
-            }
-            const Real C = Cn, S = Sn;
-            if (k > k0) {
-                const int64_t rowi = (int64_t)(k - 1 - k0) * a.orbits + o;
-                const Real *row = seg + rowi * (2 * n);
-                load_units<Real, 1, P>(row, units, u0, rn);
-                load_units<Real, 1, P>(row + n, units, u0, zn);
-                Cn = seg_sums[2 * rowi];
-                Sn = seg_sums[2 * rowi + 1];
-            }
             // Padding units: their lambda stays 0 (it starts at 0 and its
             // update is scaled by live), so they add nothing to A, B or the
             // gradients; C and S are the replay's, padding already excluded.
-            Real sn[P], cs[P];
+            Real sn[P], cs[P], z[P], C, S;
+            if constexpr (SMEM) {
+                const typename SR::Vec *row = vrec + (int)(k - k0) * NV * kForwardBlock;
+#pragma unroll
+                for (int v = 0; v < P / V; ++v) {
+                    const typename SR::Vec vs = row[v * kForwardBlock], vc = row[(P / V + v) * kForwardBlock],
+                                           vz = row[(2 * P / V + v) * kForwardBlock];
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        sn[v * V + j] = vs.v[j];
+                        cs[v * V + j] = vc.v[j];
+                        z[v * V + j] = vz.v[j];
+                    }
+                }
+                const typename SR::Pair cs2 = prec[(int)(k - k0) * kForwardBlock];
+                C = cs2.v[0];
+                S = cs2.v[1];
+            } else {
+                Real r[P];
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    r[i] = rn[0][i];
+                    z[i] = zn[0][i];
+                }
+                C = Cn;
+                S = Sn;
+                if (k > k0) load_record(seg, seg_sums, k - 1 - k0, a.orbits, o, n, units, u0, rn, zn, Cn, Sn);
+#pragma unroll
+                for (int i = 0; i < P; ++i) sincos_reduced(r[i], sn[i], cs[i]);
+            }
             Real A = 0, B = 0;
 #pragma unroll
             for (int i = 0; i < P; ++i) {
-                sincos_reduced(r[0][i], sn[i], cs[i]);
                 A = fma_r(lam[0][i], cs[i], A);
                 B = fma_r(lam[0][i], sn[i], B);
             }
             A = group_sum<G>(A);
             B = group_sum<G>(B);
+            // parameter gradients use lambda^{k+1}:
+            // sum_i lambda_i (S cos x_i - C sin x_i) = S A - C B, the same in every lane of the group
+            g_k = fma_r(S, A, fma_r(-C, B, g_k));
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 const Real l = lam[0][i];
-                // parameter gradients use lambda^{k+1}
-                g_k = fma_r(l, fma_r(S, cs[i], -mul_r(C, sn[i])), g_k);
                 g_omega[i] += l;
-                g_noise[PAPER ? i : 0] = fma_r(l, z[0][i], g_noise[PAPER ? i : 0]);
-                // lambda^k
-                const Real jac = fma_r(cs[i], A, mul_r(sn[i], B)) - l * fma_r(cs[i], C, mul_r(sn[i], S));
+                g_noise[PAPER ? i : 0] = fma_r(l, z[i], g_noise[PAPER ? i : 0]);
+                // lambda^k: cos x_l (A - lambda_l C) + sin x_l (B - lambda_l S)
+                const Real jac = fma_r(cs[i], fma_r(-l, C, A), mul_r(sn[i], fma_r(-l, S, B)));
                 lam[0][i] = fma_r(kdt_n_live[i], jac, l);
             }
         }
     }
 
     // per-orbit gradients: p = (K, sigma, omega_1..omega_n) or (K, omega, p_1..p_n)
-    g_k = group_sum<G>(g_k);
     if (!PAPER) g_noise[0] = group_sum<G>(g_noise[0]);
     if (active && SDEB_CHECK(a.check, o < a.orbits, kChkAdjointOut, o)) {
         Real *gp = static_cast<Real *>(a.dL_dp) + o * a.d;
@@ -189,11 +261,25 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
     }
 }
 
+// Segment records in shared memory while they take at most this much per
+// block (two blocks of 128 threads per SM still fit), else in global memory.
+constexpr int64_t kAdjointSmemMax = 112 * 1024;
+
 template <bool PAPER, typename Real, int G, int P>
 cudaError_t launch_adjoint_layout(const AdjointArgs &a, cudaStream_t s) {
     const int64_t grid = (a.orbits * G + kForwardBlock - 1) / kForwardBlock;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    em_adjoint_kernel<PAPER, Real, G, P><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
+    const int64_t smem = (int64_t)a.ckpt_every * SmemRec<Real, P>::kStepBytes * kForwardBlock;
+    const bool fits = smem <= kAdjointSmemMax;
+    if (a.records == SDEB_RECORDS_SHARED && !fits) return cudaErrorNotSupported;
+    if (fits && a.records != SDEB_RECORDS_GLOBAL) {
+        cudaError_t e = cudaFuncSetAttribute(em_adjoint_kernel<PAPER, Real, G, P, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        em_adjoint_kernel<PAPER, Real, G, P, true><<<(unsigned)grid, kForwardBlock, (size_t)smem, s>>>(a);
+    } else {
+        em_adjoint_kernel<PAPER, Real, G, P, false><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

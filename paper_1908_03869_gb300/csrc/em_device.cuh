@@ -335,7 +335,7 @@ __device__ __forceinline__ void accumulate(double &x, double & /*comp*/, double 
 // end at global step multiples of kCompPeriod, so a run resumed from a
 // stored (x, c) at any step, or replayed from a checkpoint, takes the same
 // roundings.
-constexpr uint32_t kCompPeriod = 4;
+constexpr uint32_t kCompPeriod = 16;
 
 __device__ __forceinline__ void accumulate_delayed(float &, float &comp, float inc) { comp = __fsub_rn(comp, inc); }
 

@@ -416,6 +416,8 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     // two steps (more independent work between the SFU waits); FP64 keeps
     // one, its registers are already near the limit.
     constexpr bool kDelayed = SCHEME == kSchemeEm && M::kDelayedComp;
+    constexpr uint32_t kRunChunk = 8;
+    static_assert(kCompPeriod % kRunChunk == 0, "a compensation period is whole chunks");
     constexpr int kRunUnroll = kKahan ? 2 : 1;
     uint32_t k = a.k_begin;
     while (k < a.k_end) {
@@ -424,10 +426,14 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
         if (ckpt != nullptr) k_stop = min(k_stop, (uint64_t)k + to_ckpt);
         if constexpr (kDelayed) k_stop = min(k_stop, (uint64_t)((k | (kCompPeriod - 1u)) + 1u));
         const uint32_t run = (uint32_t)(k_stop - k);
-        if (kDelayed && run == kCompPeriod) {
+        if (kDelayed && run % kRunChunk == 0) {
+            // whole chunks of a fixed trip count: a compensation period, or
+            // the stretches between checkpoints kept every kRunChunk steps
+            for (uint32_t s0 = 0; s0 < run; s0 += kRunChunk) {
 #pragma unroll 2
-            for (uint32_t s = 0; s < kCompPeriod; ++s)
-                em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+                for (uint32_t s = 0; s < kRunChunk; ++s)
+                    em_step<M, Real, P>(model, x, cp, k + s0 + s, noise, u0, units, a.keys, reduce);
+            }
         } else {
 #pragma unroll kRunUnroll
             for (uint32_t s = 0; s < run; ++s) {

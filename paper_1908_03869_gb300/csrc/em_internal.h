@@ -118,6 +118,7 @@ struct AdjointArgs {
     PhiloxKeys keys;
     int64_t nckpt;             // checkpoints in ckpt
     unsigned long long *check; // bounds-check status word (checked build), or null
+    int32_t records;           // SDEB_RECORDS_*: where the replay keeps a segment's records
 };
 
 cudaError_t launch_adjoint(const AdjointArgs &a, Layout l, bool fp64, cudaStream_t s);

@@ -36,6 +36,7 @@ struct sdeb_ctx {
     float *d_ckpt_comp = nullptr;
     int64_t nckpt = 0;
     int64_t ckpt_int = 0;         // checkpoint interval kept (<= pb.ckpt_every; see checkpoint_interval)
+    int32_t adj_records = SDEB_RECORDS_AUTO;  // sdeb_set_adjoint_records
     uint8_t *d_flags = nullptr;
     void *d_seg = nullptr;        // adjoint: replayed phases and normals of one segment
     void *d_gradp = nullptr;      // adjoint: per-orbit parameter gradients (shared params)
@@ -686,17 +687,30 @@ sdeb_status sdeb_create_user(const sdeb_problem *pb, const char *source, sdeb_ct
 namespace {
 
 // Checkpoint interval of a context that keeps checkpoints for sdeb_grad.
-// The adjoint replays one segment (the steps between two checkpoints) into a
-// buffer of phases and normals, 2 n elements per orbit and step, that its
-// reverse sweep reads back; with every resident orbit's segment at once in
-// flight, a segment of ckpt_every steps can outgrow the L2 cache and make
-// the buffer an HBM round trip.  The interval is then cut to ckpt_every / m
-// (m <= 16, so at most 16x the checkpoints asked for) until the in-flight
-// buffer fits a third of the L2.
+// The adjoint replays one segment (the steps between two checkpoints) and
+// keeps a record of each step for its reverse sweep.  Segments of
+// kSmemSegment steps keep the records in the shared memory of the thread
+// that writes and reads them; that interval is taken whenever its
+// checkpoints fit a quarter of the device memory.  Otherwise the records go
+// through a global buffer of 2 n + 2 elements per orbit and step; with every
+// resident orbit's segment at once in flight, a segment of ckpt_every steps
+// can outgrow the L2 cache and make the buffer an HBM round trip, so the
+// interval is cut to ckpt_every / m (m <= 16, so at most 16x the
+// checkpoints asked for) until the in-flight buffer fits 60 % of the L2.
+constexpr int64_t kSmemSegment = 8;
+
 int64_t checkpoint_interval(const sdeb_problem *pb, int32_t units, size_t elem, int device) {
     const int64_t every = pb->ckpt_every;
     const bool adjoint = every > 0 && (pb->model == SDEB_KURAMOTO || pb->model == SDEB_KURAMOTO_PAPER);
-    if (!adjoint) return every;
+    if (!adjoint || every <= kSmemSegment) return every;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const double nck = (double)((pb->steps + kSmemSegment - 1) / kSmemSegment + 1);
+        const double bytes = nck * (double)pb->orbits * (double)pb->n * (double)elem * (elem == 4 ? 2.0 : 1.0);
+        if (bytes <= (double)total_b / 4.0) return kSmemSegment;
+    } else {
+        cudaGetLastError();
+    }
     int l2 = 0, sms = 0;
     if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || l2 <= 0 || sms <= 0) {
@@ -707,13 +721,13 @@ int64_t checkpoint_interval(const sdeb_problem *pb, int32_t units, size_t elem, 
     default_layout(units, l);
     const int64_t resident = std::min<int64_t>(pb->orbits, (int64_t)sms * 2048 / l.G);
     const double per_step = (double)resident * (pb->n + 1) * 2.0 * (double)elem;
-    const int64_t fit = std::max<int64_t>(1, (int64_t)((double)l2 / 2.0 / per_step));
+    const int64_t fit = std::max<int64_t>(1, (int64_t)(0.6 * (double)l2 / per_step));
     if (fit >= every) return every;
     const int64_t m = std::min<int64_t>(16, (every + fit - 1) / fit);
     int64_t interval = (every + m - 1) / m;
-    // a multiple of 4 when possible: the FP32 forward's compensation periods
-    // then never split at a checkpoint
-    if (interval > 4) interval -= interval % 4;
+    // a multiple of the FP32 forward's compensation period when possible:
+    // the periods then never split at a checkpoint
+    if (interval > (int64_t)kCompPeriod) interval -= interval % kCompPeriod;
     return interval;
 }
 
@@ -1181,6 +1195,7 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
             g.keys = a.keys;
             g.nckpt = ctx->nckpt;
             g.check = a.check;
+            g.records = ctx->adj_records;
             float ms_adj = 0.0f;
             // checkpoints 1 .. of the trial: copies of checkpoint 0
             const int64_t ck_used = (adj_steps + ctx->ckpt_int - 1) / ctx->ckpt_int;
@@ -1222,6 +1237,15 @@ sdeb_status sdeb_autotune(sdeb_ctx *ctx, int64_t trial_steps, void *stream) {
         return cuda_fail(ctx, e, "sdeb_autotune");
     }
     ctx->layout = best;
+    return SDEB_OK;
+}
+
+sdeb_status sdeb_set_adjoint_records(sdeb_ctx *ctx, int32_t mode) {
+    if (!ctx) return fail(nullptr, SDEB_EINVAL, "ctx is NULL");
+    if (ctx->is_batch) return fail(ctx, SDEB_EINVAL, "a batch has no adjoint");
+    if (mode != SDEB_RECORDS_AUTO && mode != SDEB_RECORDS_GLOBAL && mode != SDEB_RECORDS_SHARED)
+        return fail(ctx, SDEB_EINVAL, "records mode %d is not SDEB_RECORDS_AUTO, _GLOBAL or _SHARED", mode);
+    ctx->adj_records = mode;
     return SDEB_OK;
 }
 
@@ -1283,11 +1307,13 @@ sdeb_status sdeb_grad(sdeb_ctx *ctx, const void *dL_dxK, void *dL_dp, void *dL_d
     a.keys = philox_key_schedule(ctx->pb.seed);
     a.nckpt = ctx->nckpt;
     a.check = check_word();
+    a.records = ctx->adj_records;
     const bool fp64 = ctx->pb.precision == SDEB_FP64;
     const cudaStream_t s = as_stream(stream);
     cudaError_t e = launch_adjoint(a, ctx->layout, fp64, s);
     if (e == cudaErrorNotSupported)
-        return fail(ctx, SDEB_EUNSUPPORTED, "no adjoint kernel for layout G=%d P=%d", ctx->layout.G, ctx->layout.P);
+        return fail(ctx, SDEB_EUNSUPPORTED, "no adjoint kernel for layout G=%d P=%d%s", ctx->layout.G,
+                    ctx->layout.P, ctx->adj_records == SDEB_RECORDS_SHARED ? " with records in shared memory" : "");
     if (e == cudaSuccess && shared) e = launch_sum_over_orbits(ctx->d_gradp, ctx->pb.orbits, ctx->pb.d, fp64, dL_dp, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
     return SDEB_OK;

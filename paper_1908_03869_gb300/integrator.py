@@ -11,7 +11,7 @@ import torch
 from . import (SDEB_FLAG_NO_FRAMES, SDEB_FLAG_SHARED_PARAMS, SDEB_FP64, SDEB_MEM_DEVICE, SDEB_MEM_HOST,
                SDEB_MEM_HOST_ASYNC, Problem, sdeb_autotune, sdeb_create,
                sdeb_destroy, sdeb_frame_moments, sdeb_get_layout, sdeb_grad, sdeb_integrate, sdeb_integrate_range, sdeb_orbit_flags,
-               sdeb_read_final, sdeb_read_orbits, sdeb_set_layout, sdeb_set_params)
+               sdeb_read_final, sdeb_read_orbits, sdeb_set_adjoint_records, sdeb_set_layout, sdeb_set_params)
 
 
 def _ptr(t):
@@ -87,6 +87,11 @@ class Integrator:
 
     def layout(self):
         return sdeb_get_layout(self.ctx)
+
+    def set_adjoint_records(self, mode):
+        """Where grad()'s replay keeps its step records: SDEB_RECORDS_AUTO,
+        _GLOBAL or _SHARED."""
+        sdeb_set_adjoint_records(self.ctx, mode)
 
     def autotune(self, trial_steps=0, stream=None):
         """Pick the fastest lane-group layout (after set_params, before integrating)."""

@@ -91,10 +91,11 @@ def test_adjoint_matches_oracle(precision, model, n, ckpt):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_adjoint_with_a_shortened_checkpoint_interval(precision):
-    """Many orbits of n = 128: the segment buffer for ckpt_every = 97 would
-    outgrow a third of the L2, so the context keeps checkpoints more often
-    (an interval that does not divide the 302 steps: a ragged last
-    segment).  Sampled orbits' gradients against the oracle adjoint."""
+    """Many orbits of n = 128 with ckpt_every = 97: the context keeps
+    checkpoints every 8 steps (an interval that does not divide the 302
+    steps: a ragged last segment); at the default layout (16 lanes of 8
+    units) the FP32 records fit shared memory, the FP64 ones go through the
+    global buffer.  Sampled orbits' gradients against the oracle adjoint."""
     import torch
     from paper_1908_03869_gb300.integrator import Integrator
 
@@ -111,7 +112,7 @@ def test_adjoint_with_a_shortened_checkpoint_interval(precision):
         dp, dx0 = it.grad(torch.tensor(c, dtype=dt_t).cuda())
         dp, dx0 = dp.cpu().numpy(), dx0.cpu().numpy()
     print("checkpoint interval", interval)
-    assert 0 < interval < ckpt and steps % interval != 0
+    assert interval == 8 and steps % interval != 0
     m, d = sdeb.model_shape("kuramoto", n)
     opb = oracle.make_problem("kuramoto", n, m, d, dt, steps, 1, seed)
     tol = 1e-10 if precision == "fp64" else 1e-3
@@ -333,3 +334,61 @@ def test_autotune_on_a_checkpointed_context_keeps_the_gradient_consistent():
     dp_o, dx0_o = oracle.adjoint(opb, p.astype(np.float64), x0.astype(np.float64), dL.astype(np.float64))
     assert _rel(res[0][1], dp_o) < 1e-3
     assert _rel(res[0][2], dx0_o) < 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_adjoint_records_in_shared_and_global_memory_agree(precision):
+    """The replay's step records kept in shared memory or in the global
+    buffer (sdeb_set_adjoint_records) give the same bits, at layouts whose
+    records fit shared memory at the 8-step interval; SHARED where they do
+    not fit (FP64 with 8 units per lane) is EUNSUPPORTED.  A context asked
+    for checkpoints at most 6 steps apart keeps them every 6 steps.  The
+    gradients against the oracle adjoint (ragged last segment: 250 steps)."""
+    import torch
+    from paper_1908_03869_gb300.integrator import Integrator
+
+    n, orbits, dt, steps, seed = 32, 300, 0.01, 250, 5
+    p, x0 = inputs.kuramoto(n, orbits, seed=11)
+    p, x0 = p.astype(np_dtype(precision)).astype(np.float64), x0.astype(np_dtype(precision)).astype(np.float64)
+    c = np.random.Generator(np.random.PCG64(12)).standard_normal((orbits, n))
+    dt_t = torch.float64 if precision == "fp64" else torch.float32
+    m, d = sdeb.model_shape("kuramoto", n)
+    opb = oracle.make_problem("kuramoto", n, m, d, dt, steps, 1, seed)
+    tol = 1e-10 if precision == "fp64" else 1e-3
+    samples = (0, 151, 299)
+    ref = [oracle.adjoint(opb, p[o:o + 1], x0[o:o + 1], c[o:o + 1], orbit_begin=o) for o in samples]
+    for ckpt in (100, 6):
+        for lay in ((8, 4), (4, 8)):
+            # a block's records: interval x (3 P + 2) elements x 128 threads, shared memory up to 112 KB
+            elem = 8 if precision == "fp64" else 4
+            fits = min(ckpt, 8) * (3 * lay[1] + 2) * 128 * elem <= 112 * 1024
+            res = {}
+            for mode in (sdeb.SDEB_RECORDS_AUTO, sdeb.SDEB_RECORDS_GLOBAL, sdeb.SDEB_RECORDS_SHARED):
+                pb = sdeb.Problem.make("kuramoto", n, orbits, dt, steps, 1, seed, precision, ckpt_every=ckpt,
+                                       no_frames=True)
+                with Integrator(pb) as it:
+                    assert sdeb.sdeb_get_checkpoint_interval(it.ctx) == min(ckpt, 8)
+                    it.set_params(torch.tensor(p, dtype=dt_t).cuda(), torch.tensor(x0, dtype=dt_t).cuda())
+                    it.set_layout(*lay)
+                    it.set_adjoint_records(mode)
+                    it.integrate()
+                    dL = torch.tensor(c, dtype=dt_t).cuda()
+                    if mode == sdeb.SDEB_RECORDS_SHARED and not fits:
+                        with pytest.raises(sdeb.SdebError) as e:
+                            it.grad(dL)
+                        assert e.value.status == sdeb.SDEB_EUNSUPPORTED
+                        continue
+                    dp, dx0 = it.grad(dL)
+                    res[mode] = (dp.cpu().numpy(), dx0.cpu().numpy())
+            for mode, (dp, dx0) in res.items():
+                np.testing.assert_array_equal(dp, res[sdeb.SDEB_RECORDS_GLOBAL][0], err_msg=str((ckpt, lay, mode)))
+                np.testing.assert_array_equal(dx0, res[sdeb.SDEB_RECORDS_GLOBAL][1], err_msg=str((ckpt, lay, mode)))
+            dp, dx0 = res[sdeb.SDEB_RECORDS_AUTO]
+            for o, (rdp, rdx0) in zip(samples, ref):
+                assert _rel(dp[o:o + 1], rdp) < tol, (ckpt, lay, o)
+                assert _rel(dx0[o:o + 1], rdx0) < tol, (ckpt, lay, o)
+    with pytest.raises(sdeb.SdebError) as e:
+        pb = sdeb.Problem.make("kuramoto", n, orbits, dt, steps, 1, seed, precision, ckpt_every=10, no_frames=True)
+        with Integrator(pb) as it:
+            it.set_adjoint_records(7)
+    assert e.value.status == sdeb.SDEB_EINVAL
