@@ -142,6 +142,10 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
 #pragma unroll
             for (int i = 0; i < P; ++i) cp[0][i] = Real(0);
         }
+        // FP32 replays two steps per iteration, as the forward does (more
+        // independent work between the special-function unit's waits)
+        constexpr int kReplayUnroll = sizeof(Real) == 4 ? 2 : 1;
+#pragma unroll kReplayUnroll
         for (uint32_t k = k0; k < k1; ++k) {
             StepRecord<Real, P> rec;
             em_step<M, Real, P, true>(model, x, cp, k, noise, u0, units, a.keys, reduce, &rec);

@@ -369,6 +369,15 @@ __device__ __forceinline__ void implicit_step(M &model, Real (&x)[M::U][P], Real
 // Step schemes of the forward kernel.
 enum : int { kSchemeEm = 0, kSchemeRk4 = 1, kSchemeImplicit = 2 };
 
+// Blocks per SM the forward kernel's registers are capped for (0: the
+// compiler's choice); see em_forward_kernel_capped.
+template <class M, typename Real, int G, int P, int SCHEME>
+constexpr int kForwardMinBlocks =
+    !(std::is_same<Real, float>::value && G > 1 && M::U == 1 && P <= 8) ? 0
+    : SCHEME == kSchemeEm ? (P <= 4 ? 7 : 5)
+    : SCHEME == kSchemeImplicit ? 5
+    : 0;
+
 template <class M, typename Real, int G, int P, int SCHEME>
 __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     constexpr int U = M::U;
@@ -416,8 +425,9 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
     // two steps (more independent work between the SFU waits); FP64 keeps
     // one, its registers are already near the limit.
     constexpr bool kDelayed = SCHEME == kSchemeEm && M::kDelayedComp;
-    constexpr uint32_t kRunChunk = 8;
-    static_assert(kCompPeriod % kRunChunk == 0, "a compensation period is whole chunks");
+    constexpr uint32_t kRunShort = 8;
+    static_assert(kCompPeriod % kRunShort == 0, "a compensation period is whole chunks");
+    constexpr bool kChunkRuns = kForwardMinBlocks<M, Real, G, P, SCHEME> == 0;
     constexpr int kRunUnroll = kKahan ? 2 : 1;
     uint32_t k = a.k_begin;
     while (k < a.k_end) {
@@ -426,15 +436,35 @@ __device__ __forceinline__ void em_forward_body(const ForwardArgs &a) {
         if (ckpt != nullptr) k_stop = min(k_stop, (uint64_t)k + to_ckpt);
         if constexpr (kDelayed) k_stop = min(k_stop, (uint64_t)((k | (kCompPeriod - 1u)) + 1u));
         const uint32_t run = (uint32_t)(k_stop - k);
-        if (kDelayed && run % kRunChunk == 0) {
-            // whole chunks of a fixed trip count: a compensation period, or
-            // the stretches between checkpoints kept every kRunChunk steps
-            for (uint32_t s0 = 0; s0 < run; s0 += kRunChunk) {
+        bool fixed = false;  // the run went through a loop of fixed trip count
+        if constexpr (kDelayed && kChunkRuns) {
+            // whole 8-step chunks (a compensation period is two): kernels
+            // without a register cap
+            if (run % kRunShort == 0) {
+                for (uint32_t s0 = 0; s0 < run; s0 += kRunShort) {
 #pragma unroll 2
-                for (uint32_t s = 0; s < kRunChunk; ++s)
-                    em_step<M, Real, P>(model, x, cp, k + s0 + s, noise, u0, units, a.keys, reduce);
+                    for (uint32_t s = 0; s < kRunShort; ++s)
+                        em_step<M, Real, P>(model, x, cp, k + s0 + s, noise, u0, units, a.keys, reduce);
+                }
+                fixed = true;
             }
-        } else {
+        } else if constexpr (kDelayed) {
+            // a whole compensation period, or the stretch between
+            // checkpoints kept every kRunShort steps: capped kernels keep
+            // the loop without an outer level (no spills within the cap)
+            if (run == kCompPeriod) {
+#pragma unroll 2
+                for (uint32_t s = 0; s < kCompPeriod; ++s)
+                    em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+                fixed = true;
+            } else if (run == kRunShort) {
+#pragma unroll 2
+                for (uint32_t s = 0; s < kRunShort; ++s)
+                    em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+                fixed = true;
+            }
+        }
+        if (!fixed) {
 #pragma unroll kRunUnroll
             for (uint32_t s = 0; s < run; ++s) {
                 if constexpr (SCHEME == kSchemeRk4)
@@ -514,20 +544,17 @@ __global__ void __launch_bounds__(kForwardBlock) em_forward_kernel(const Forward
     em_forward_body<M, Real, G, P, SCHEME>(a);
 }
 
-// The same kernel with registers capped so that five blocks fit per SM: used
-// for FP32 one-component models on multi-lane layouts with up to 8 units per
-// lane, which fit 96 registers without spilling and ran 2-3 % faster than at
-// the compiler's choice (128 registers, four blocks).  The implicit schemes
-// use it too (a few spilled words, 1 % faster than four blocks); Runge-Kutta
-// fits 96 registers by itself.  The single-lane layouts keep the compiler's
-// choice (96 registers already).
-template <class M, typename Real, int G, int P, int SCHEME>
-__global__ void __launch_bounds__(kForwardBlock, 5) em_forward_kernel_5blocks(const ForwardArgs a) {
+// The same kernel with registers capped so that MINB blocks fit per SM,
+// for FP32 one-component models on multi-lane layouts: 4 units per lane fit
+// 72 registers (seven blocks), 8 units 96 registers (five blocks) without
+// spilling; both ran faster than at the compiler's choice (96 and 128
+// registers: five and four blocks).  The implicit schemes take five blocks
+// (a few spilled words, 1 % faster than four); Runge-Kutta fits 96
+// registers by itself.  The single-lane layouts keep the compiler's choice.
+template <class M, typename Real, int G, int P, int SCHEME, int MINB>
+__global__ void __launch_bounds__(kForwardBlock, MINB) em_forward_kernel_capped(const ForwardArgs a) {
     em_forward_body<M, Real, G, P, SCHEME>(a);
 }
-
-template <class M, typename Real, int G, int P>
-constexpr bool kForwardFiveBlocks = std::is_same<Real, float>::value && G > 1 && M::U == 1 && P <= 8;
 
 // SCHEME: kSchemeEm (Euler-Maruyama, or Milstein chosen by the model
 // functor), or an ODE-path scheme (kSchemeRk4, kSchemeImplicit).
@@ -537,8 +564,9 @@ cudaError_t launch_forward_layout(const ForwardArgs &a, cudaStream_t s) {
     const int64_t threads = a.orbits * G;
     const int64_t grid = (threads + kForwardBlock - 1) / kForwardBlock;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if constexpr ((SCHEME == kSchemeEm || SCHEME == kSchemeImplicit) && kForwardFiveBlocks<M, Real, G, P>)
-        em_forward_kernel_5blocks<M, Real, G, P, SCHEME><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
+    constexpr int minb = kForwardMinBlocks<M, Real, G, P, SCHEME>;
+    if constexpr (minb > 0)
+        em_forward_kernel_capped<M, Real, G, P, SCHEME, minb><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     else
         em_forward_kernel<M, Real, G, P, SCHEME><<<(unsigned)grid, kForwardBlock, 0, s>>>(a);
     return cudaGetLastError();
