@@ -120,27 +120,48 @@ __global__ void __launch_bounds__(kForwardBlock) em_adjoint_kernel(const Adjoint
     const NoiseLane<P> noise(gorb, u0, a.keys);
     const int64_t nseg = ((int64_t)a.steps + a.ckpt_every - 1) / a.ckpt_every;
 
+    // Checkpoint c's state (and FP32 compensation) into (cx, ccp).
+    auto load_ckpt = [&](int64_t c, Real (&cx)[1][P], Real (&ccp)[1][P]) {
+        if (SDEB_CHECK(a.check, c < a.nckpt, kChkAdjointCkpt, c)) {
+            load_units<Real, 1, P>(ckpt + (c * a.orbits + o) * n, units, u0, cx);
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) cx[0][i] = Real(0);
+        }
+        if constexpr (std::is_same<Real, float>::value) {
+            if (c < a.nckpt) {
+                load_units<float, 1, P>(a.ckpt_comp + (c * a.orbits + o) * n, units, u0, ccp);
+            } else {
+#pragma unroll
+                for (int i = 0; i < P; ++i) ccp[0][i] = 0.0f;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) ccp[0][i] = Real(0);
+        }
+    };
+    // FP32: the next segment's checkpoint is loaded one segment ahead, so
+    // its memory latency passes under the current segment instead of
+    // stalling every warp at the segment's start (FP64 has no registers to
+    // spare and loads at the start).
+    constexpr bool kPrefetch = sizeof(Real) == 4;
+    Real xn[1][P], cpn[1][P];
+    if constexpr (kPrefetch) load_ckpt(nseg - 1, xn, cpn);
+
     for (int64_t c = nseg - 1; c >= 0; --c) {
         const uint32_t k0 = (uint32_t)(c * a.ckpt_every);
         const uint32_t k1 = (uint32_t)((int64_t)k0 + a.ckpt_every < (int64_t)a.steps ? k0 + a.ckpt_every : a.steps);
         // ---- replay the segment from its checkpoint --------------------------
         Real x[1][P], cp[1][P];
-        if (SDEB_CHECK(a.check, c < a.nckpt, kChkAdjointCkpt, c)) {
-            load_units<Real, 1, P>(ckpt + (c * a.orbits + o) * n, units, u0, x);
-        } else {
+        if constexpr (kPrefetch) {
 #pragma unroll
-            for (int i = 0; i < P; ++i) x[0][i] = Real(0);
-        }
-        if constexpr (std::is_same<Real, float>::value) {
-            if (c < a.nckpt) {
-                load_units<float, 1, P>(a.ckpt_comp + (c * a.orbits + o) * n, units, u0, cp);
-            } else {
-#pragma unroll
-                for (int i = 0; i < P; ++i) cp[0][i] = 0.0f;
+            for (int i = 0; i < P; ++i) {
+                x[0][i] = xn[0][i];
+                cp[0][i] = cpn[0][i];
             }
+            if (c > 0) load_ckpt(c - 1, xn, cpn);
         } else {
-#pragma unroll
-            for (int i = 0; i < P; ++i) cp[0][i] = Real(0);
+            load_ckpt(c, x, cp);
         }
         // FP32 replays two steps per iteration, as the forward does (more
         // independent work between the special-function unit's waits)
