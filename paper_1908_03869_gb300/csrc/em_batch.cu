@@ -67,45 +67,46 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
     const uint32_t steps = in.steps;
     uint32_t to_frame = in.stride;
     // Steps run in runs that end at the next event (a frame or the end) of
-    // any item of the warp, so the step loop carries no per-step checks; the
-    // run length is the warp's minimum, the same in every warp of a team.
+    // any item of the warp, or at the end of a compensation period, so the
+    // step loop carries no per-step checks; the run length is the warp's
+    // minimum, the same in every warp of a team.  A whole period runs as a
+    // loop of fixed trip count (one step per iteration: two would spill
+    // within the kernel's 96 registers).
     uint32_t k = 0;
     while (k < kmax) {
         const bool live = has && k < steps;
         uint32_t mine = kmax - k;
         if (live) mine = min(mine, min(to_frame, steps - k));
+        if constexpr (M::kDelayedComp) mine = min(mine, ((k | (kCompPeriod - 1u)) + 1u) - k);
         const uint32_t run = __reduce_min_sync(0xffffffffu, mine);
+        if constexpr (SHARE_PHILOX) {
+            // Lanes 2b and 2b + 1 (units 4b.. and 4b + 2..) use the two
+            // halves of noise block b: over a pair of steps each lane draws
+            // the block for one of the steps (the even lane step k, the odd
+            // lane step k + 1) and hands its partner the half the partner
+            // uses, so a block costs one Philox call per step instead of two.
+            const bool odd = (lane & 1) != 0;
+            uint32_t s = 0;
 #pragma unroll 1
-        for (uint32_t s = 0; s < run;) {
-            if constexpr (SHARE_PHILOX) {
-                // Lanes 2b and 2b + 1 (units 4b.. and 4b + 2..) use the two
-                // halves of noise block b: over a pair of steps each lane
-                // draws the block for one of the steps (the even lane step
-                // k, the odd lane step k + 1) and hands its partner the half
-                // the partner uses, so a block costs one Philox call per
-                // step instead of two.
-                if (s + 2 <= run) {
-                    const bool odd = (lane & 1) != 0;
-                    const U32x4 w = philox4x32_10_fixed(k + s + (odd ? 1u : 0u), noise.r1[0], a.keys);
-                    const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? w.x : w.z, 1);
-                    const uint32_t r1 = __shfl_xor_sync(0xffffffffu, odd ? w.y : w.w, 1);
-                    em_step_words<M, Real>(model, x, cp, odd ? r0 : w.x, odd ? r1 : w.y, u0, units, reduce);
-                    if constexpr (M::kDelayedComp) {
-                        if (((k + s + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
-                    }
-                    em_step_words<M, Real>(model, x, cp, odd ? w.z : r0, odd ? w.w : r1, u0, units, reduce);
-                    if constexpr (M::kDelayedComp) {
-                        if (((k + s + 2u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
-                    }
-                    s += 2;
-                    continue;
-                }
+            for (; s + 2 <= run; s += 2) {
+                const U32x4 w = philox4x32_10_fixed(k + s + (odd ? 1u : 0u), noise.r1[0], a.keys);
+                const uint32_t r0 = __shfl_xor_sync(0xffffffffu, odd ? w.x : w.z, 1);
+                const uint32_t r1 = __shfl_xor_sync(0xffffffffu, odd ? w.y : w.w, 1);
+                em_step_words<M, Real>(model, x, cp, odd ? r0 : w.x, odd ? r1 : w.y, u0, units, reduce);
+                em_step_words<M, Real>(model, x, cp, odd ? w.z : r0, odd ? w.w : r1, u0, units, reduce);
             }
-            em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
-            if constexpr (M::kDelayedComp) {
-                if (((k + s + 1u) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
-            }
-            ++s;
+            if (s < run) em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+        } else if (M::kDelayedComp && run == kCompPeriod) {
+#pragma unroll 1
+            for (uint32_t s = 0; s < kCompPeriod; ++s)
+                em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+        } else {
+#pragma unroll 1
+            for (uint32_t s = 0; s < run; ++s)
+                em_step<M, Real, P>(model, x, cp, k + s, noise, u0, units, a.keys, reduce);
+        }
+        if constexpr (M::kDelayedComp) {
+            if (((k + run) & (kCompPeriod - 1u)) == 0) renormalize_units(x, cp);
         }
         k += run;
         if (live) {
