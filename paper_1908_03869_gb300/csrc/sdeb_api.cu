@@ -248,30 +248,42 @@ cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream
 
 // ---- batch planning ---------------------------------------------------------
 
-// Thread-instructions per lane per step for a lane holding P units: the
-// phase, sums and update of every unit, the normals (a lane with fewer than
-// four units still draws a whole Philox block), the lane's share of the
-// coupling-sum exchange (segmented scan in a packed warp; butterfly plus
-// shared memory and a barrier in a team) and the loop.
-double batch_step_cost(int P, bool team) { return P * 28.0 + std::max(P, 4) / 4 * 38.0 + (team ? 43.0 : 30.0); }
+// Time of one step of a lane group, in ns, as measured on the 4096-instance
+// workload with three resident blocks per SM (median over the tasks of each
+// kind, from a per-task timeline): a packed warp with P = 8 / 4 units per
+// lane 650 / 425, a 64-lane team with 4 units per lane 388, a team with 2
+// units per lane 227 (128 lanes) to 249 (64).  A packed warp's step is not
+// much shorter with fewer units per lane (2 and 1: 385 and 390): with other
+// warps on its SM sub-partition its rate is set by the issue slots it gets,
+// while a team spreads an item's units over two or four sub-partitions,
+// shares its Philox blocks between lane pairs and adds its sums with one
+// redux per warp instead of a five-level scan.  An item's chain is steps x
+// this time, its work that times its lanes.
+double batch_step_cost(int P, bool team) {
+    if (team) return P == 4 ? 388.0 : 240.0;
+    return P == 8 ? 650.0 : 425.0;
+}
 
 // Where an item runs: a packed warp with P = 8 or 4 units per lane on
-// ceil(units / P) <= 32 lanes, or a team of 64 lanes (P = 4 or 2) or 128
-// lanes (P = 2).  An item takes the layout of least total work (lanes x
-// per-step cost) among those whose sequential chain, steps x per-step cost,
-// stays within chain_max, else the layout with the shortest chain.
+// ceil(units / P) <= 32 lanes, or a team of 64 lanes (P = 4 for more than
+// 64 units, P = 2 for up to 128) or 128 lanes (P = 2, more than 128 units).
+// An item takes the layout of least total work (lanes x per-step cost)
+// among those whose sequential chain, steps x per-step cost, stays within
+// chain_max, else the layout with the shortest chain.  A small item on a
+// 64-lane team leaves most lanes idle, but its chain is the shortest it can
+// have, which is what the longest instances of small n need.
 struct ItemLayout {
     int lanes = 0, P = 0;
     bool team = false;
 };
 
 ItemLayout choose_item_layout(int units, uint32_t steps, double chain_max) {
-    ItemLayout cand[7];
+    ItemLayout cand[5];
     int nc = 0;
     for (int P : {8, 4})
         if ((units + P - 1) / P <= 32) cand[nc++] = {(units + P - 1) / P, P, false};
-    for (int P : {4, 2})
-        if (units <= 64 * P && units > 16 * P) cand[nc++] = {64, P, true};
+    if (units > 64 && units <= 256) cand[nc++] = {64, 4, true};
+    if (units <= 128) cand[nc++] = {64, 2, true};
     if (units > 128 && units <= 256) cand[nc++] = {128, 2, true};
     ItemLayout best, shortest;
     double best_work = 0.0, shortest_chain = 0.0;
@@ -298,10 +310,10 @@ struct BatchPlan {
 };
 
 BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, int num_sms) {
-    double total_warp_instr = 0.0;
+    double total_warp_time = 0.0;   // the whole batch in packed warps of 8 units per lane
     for (const BatchInstance &b : inst)
-        total_warp_instr += (double)b.steps * b.orbits * b.units * batch_step_cost(8, false) / 8.0 / 32.0;
-    const double chain_max = chain_frac * total_warp_instr / (4.0 * std::max(1, num_sms));
+        total_warp_time += (double)b.steps * b.orbits * b.units * batch_step_cost(8, false) / 8.0 / 32.0;
+    const double chain_max = chain_frac * total_warp_time / (4.0 * std::max(1, num_sms));
     struct Cand {
         int32_t instance, orbit;
         uint32_t steps;
@@ -524,7 +536,7 @@ sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
     bool first = true;
     const int cap = c->grid_cap;
     for (double frac : {0.125, 0.25, 0.5, 1.0, 2.0})
-      for (int per_sm : {2, 3, 4}) {
+      for (int per_sm : {2, 3, 4, 5}) {
         if (e != cudaSuccess) break;
         c->grid_cap = std::min(cap, per_sm * c->num_sms);
         if (upload_plan(c, plan_batch(c->inst, frac, c->num_sms)) != SDEB_OK) {

@@ -4,8 +4,9 @@ The schedule must place every orbit exactly once; a packed warp holds items
 of one units-per-lane value side by side within 32 lanes, each on
 ceil(n / P) lanes, with step counts within a factor 1.2 of each other;
 teams hold one item on 64 or 128 lanes.  Without a chain limit nothing runs
-as a team; with the tightest limit every item takes the layout with the
-fewest units per lane that exists for its n."""
+as a team; with the tightest limit every item takes the layout of the
+shortest chain for its n, a team with 2 units per lane (64 lanes up to
+n = 128, 128 lanes above)."""
 import math
 
 import numpy as np
@@ -81,7 +82,7 @@ def test_chain_limit_extremes():
     assert (loose["slot"] <= 3).all() and (loose["lanes"] <= 32).all()
     tight = sdeb.sdeb_batch_plan(pbs, 1e-9, 152)
     for i, pb in enumerate(pbs):
-        want = (-(-pb.n // 4), 4) if pb.n <= 32 else ((64, 2) if pb.n <= 128 else (128, 2))
+        want = (64, 2) if pb.n <= 128 else (128, 2)
         assert (tight["lanes"][i], tight["units_per_lane"][i]) == want, (pb.n, pb.steps)
 
 
