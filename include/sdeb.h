@@ -200,7 +200,8 @@ SDEB_API sdeb_status sdeb_batch_info(const sdeb_ctx *ctx, int32_t *tasks, int32_
 
 /* Schedule knob of a batch (sdeb_autotune picks it by timing): each orbit
  * takes the layout of least total work -- 8 or 4 units per lane in a packed
- * warp, or a 64-lane (4 or 2 units per lane) or 128-lane (2) team --
+ * warp, a warp of its own (2 units per lane, at most 64 units), or a
+ * 64-lane (4 or 2 units per lane) or 128-lane (2) team --
  * among those whose sequential chain, steps x per-step cost, stays within
  * chain_fraction x the batch's average work per SM sub-partition, else the
  * layout with the shortest chain.  Packed warps hold several orbits side
@@ -210,8 +211,9 @@ SDEB_API sdeb_status sdeb_batch_info(const sdeb_ctx *ctx, int32_t *tasks, int32_
 SDEB_API sdeb_status sdeb_batch_set_schedule(sdeb_ctx *ctx, double chain_fraction);
 
 /* Layout the current schedule gives the orbits of `instance`: lanes per
- * orbit (ceil(n / units_per_lane) <= 32 in a packed warp, 64 or 128 for a
- * multi-warp team) and units per lane (8, 4 or 2). */
+ * orbit (ceil(n / units_per_lane) <= 32 in a packed warp or a warp of its
+ * own, 64 or 128 for a multi-warp team) and units per lane (8, 4 or 2; 2
+ * with at most 32 lanes is an orbit alone on its warp). */
 SDEB_API sdeb_status sdeb_batch_layout(const sdeb_ctx *ctx, int32_t instance, int32_t *lanes, int32_t *units_per_lane);
 
 /* Host-only view of the schedule sdeb_create_batch + sdeb_batch_set_schedule

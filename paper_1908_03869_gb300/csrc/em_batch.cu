@@ -188,6 +188,44 @@ __device__ __forceinline__ void run_packed_warp(const BatchArgs &a, const BatchW
     run_item<Real, P>(a, a.items[t.first + (has ? mine : 0)], has, lane - s, t.kmax, reduce);
 }
 
+// One item alone on a warp, 2 units per lane: the coupling sums over the
+// whole warp, FP64 by butterfly (the same bits in every lane), FP32 in the
+// 32-bit fixed point of the teams' sums (multiples of 2^-22) added by one
+// redux.sync, so an item's FP32 sums are the bits a one-warp team would
+// form.  No shared memory and no barrier.
+template <typename Real>
+struct SoloWarpSum {
+    template <int NR>
+    __device__ __forceinline__ void operator()(Real (&r)[NR]) const {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r[q] = group_sum<32>(r[q]);
+    }
+};
+
+template <>
+struct SoloWarpSum<float> {
+    template <int NR>
+    __device__ __forceinline__ void operator()(float (&r)[NR]) const {
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+            r[q] = __int2float_rn(__reduce_add_sync(0xffffffffu, __float2int_rn(r[q] * 0x1p22f))) * 0x1p-22f;
+    }
+};
+
+// A single-warp item (a warp task with p == 2 and one item): lanes 2b and
+// 2b + 1 share noise block b as a team's lane pairs do; lanes past the
+// item's ceil(n / 2) hold no units and add zeros.
+template <typename Real>
+__device__ __forceinline__ void run_solo_warp(const BatchArgs &a, const BatchWarpTask &t) {
+    if (!SDEB_CHECK(a.check, t.count == 1 && t.first >= 0 && t.first < a.nitems, kChkBatchItem, t.first)) return;
+    const BatchItem it = a.items[t.first];
+    if (!SDEB_CHECK(a.check, it.instance >= 0 && it.instance < a.ninst, kChkBatchInstance, it.instance)) return;
+    if (!SDEB_CHECK(a.check, a.inst[it.instance].units <= 64, kChkBatchLane, a.inst[it.instance].units)) return;
+    SoloWarpSum<Real> reduce;
+    run_item<Real, 2, SoloWarpSum<Real>, true>(a, it, true, (int)(threadIdx.x & 31), a.inst[it.instance].steps,
+                                               reduce);
+}
+
 // Team of NW warps on one item; BAR = 0 is the whole block's barrier,
 // otherwise named barrier BAR for the team's 32 * NW threads.
 template <int NW, int BAR, typename Real>
@@ -290,6 +328,7 @@ __global__ void __launch_bounds__(kBatchBlock, 5) em_batch_kernel(const BatchArg
             switch (wt.count > 0 ? wt.p : 0) {
             case 8: run_packed_warp<Real, 8>(a, wt); break;
             case 4: run_packed_warp<Real, 4>(a, wt); break;
+            case 2: run_solo_warp<Real>(a, wt); break;
             default: break;
             }
         } else if (task.kind == kBatchTeam128) {

@@ -132,11 +132,13 @@ cudaError_t launch_sum_over_orbits(const void *in, int64_t orbits, int32_t d, bo
 // instance.  The persistent kernel's blocks (four warps) pull tasks from a
 // queue sorted longest-first: one item on all 128 lanes of the block, two
 // items on 64 lanes each (sums exchanged through shared memory), or four
-// packed warps.  A packed warp holds several items side by side, each on
+// warps.  A packed warp holds several items side by side, each on
 // ceil(units / P) consecutive lanes (P = 8 or 4 units per lane), items of
 // similar step counts; an item's coupling sums are a segmented scan over
-// its own lanes.  Long items get fewer units per lane (teams), so the
-// longest sequential chains are spread over more lanes.
+// its own lanes.  A single-warp item (at most 64 units, 2 per lane) has the
+// warp to itself and sums with one redux.  Long items get fewer units per
+// lane (teams, single-warp items), so the longest sequential chains are
+// spread over more lanes.
 struct BatchInstance {
     int32_t n, units, d;
     int32_t param_stride;          // d, or 0 when the instance shares one parameter vector
@@ -153,7 +155,7 @@ struct BatchItem {
 };
 
 struct BatchWarpTask {
-    int16_t p;                     // units per lane: 8 or 4
+    int16_t p;                     // units per lane: 8 or 4 (packed), 2 (one item alone on the warp)
     int16_t count;                 // items in the warp, in lane order; 0 = idle warp
     int32_t first;                 // first item index
     uint32_t kmax;                 // largest step count among the warp's items

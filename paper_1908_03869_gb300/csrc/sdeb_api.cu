@@ -257,39 +257,44 @@ cudaError_t launch_forward(const ForwardArgs &a, Layout l, bool fp64, cudaStream
 // warps on its SM sub-partition its rate is set by the issue slots it gets,
 // while a team spreads an item's units over two or four sub-partitions,
 // shares its Philox blocks between lane pairs and adds its sums with one
-// redux per warp instead of a five-level scan.  An item's chain is steps x
-// this time, its work that times its lanes.
+// redux per warp instead of a five-level scan.  A single-warp item (2 units
+// per lane, sums by one redux, no barrier) is taken at a team's 240.  An
+// item's chain is steps x this time, its work that times the lanes it holds
+// (a single-warp item holds the whole warp).
 double batch_step_cost(int P, bool team) {
     if (team) return P == 4 ? 388.0 : 240.0;
-    return P == 8 ? 650.0 : 425.0;
+    return P == 8 ? 650.0 : P == 4 ? 425.0 : 240.0;
 }
 
 // Where an item runs: a packed warp with P = 8 or 4 units per lane on
-// ceil(units / P) <= 32 lanes, or a team of 64 lanes (P = 4 for more than
-// 64 units, P = 2 for up to 128) or 128 lanes (P = 2, more than 128 units).
-// An item takes the layout of least total work (lanes x per-step cost)
-// among those whose sequential chain, steps x per-step cost, stays within
-// chain_max, else the layout with the shortest chain.  A small item on a
-// 64-lane team leaves most lanes idle, but its chain is the shortest it can
-// have, which is what the longest instances of small n need.
+// ceil(units / P) <= 32 lanes, a warp of its own (P = 2, up to 64 units),
+// or a team of 64 lanes (P = 4 for more than 64 units, P = 2 for 65 to 128)
+// or 128 lanes (P = 2, more than 128 units).  An item takes the layout of
+// least total work (lanes x per-step cost) among those whose sequential
+// chain, steps x per-step cost, stays within chain_max, else the layout
+// with the shortest chain.  A small item alone on a warp leaves lanes idle,
+// but its chain is the shortest it can have, which is what the longest
+// instances of small n need.
 struct ItemLayout {
     int lanes = 0, P = 0;
     bool team = false;
+    bool solo = false;   // a warp of its own (lanes: those holding units)
 };
 
 ItemLayout choose_item_layout(int units, uint32_t steps, double chain_max) {
-    ItemLayout cand[5];
+    ItemLayout cand[6];
     int nc = 0;
     for (int P : {8, 4})
-        if ((units + P - 1) / P <= 32) cand[nc++] = {(units + P - 1) / P, P, false};
-    if (units > 64 && units <= 256) cand[nc++] = {64, 4, true};
-    if (units <= 128) cand[nc++] = {64, 2, true};
-    if (units > 128 && units <= 256) cand[nc++] = {128, 2, true};
+        if ((units + P - 1) / P <= 32) cand[nc++] = {(units + P - 1) / P, P, false, false};
+    if (units <= 64) cand[nc++] = {(units + 1) / 2, 2, false, true};
+    if (units > 64 && units <= 256) cand[nc++] = {64, 4, true, false};
+    if (units > 64 && units <= 128) cand[nc++] = {64, 2, true, false};
+    if (units > 128 && units <= 256) cand[nc++] = {128, 2, true, false};
     ItemLayout best, shortest;
     double best_work = 0.0, shortest_chain = 0.0;
     for (int c = 0; c < nc; ++c) {
         const double per_step = batch_step_cost(cand[c].P, cand[c].team);
-        const double chain = (double)steps * per_step, work = chain * cand[c].lanes;
+        const double chain = (double)steps * per_step, work = chain * (cand[c].solo ? 32 : cand[c].lanes);
         if (chain <= chain_max && (best.P == 0 || work < best_work)) {
             best = cand[c];
             best_work = work;
@@ -320,6 +325,7 @@ BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, 
         int lanes;
     };
     std::vector<Cand> packed[9];               // by units per lane (8 or 4)
+    std::vector<Cand> solo;                    // single-warp items (2 units per lane)
     std::vector<Cand> team64[5], team128[5];   // by units per lane (2 or 4)
     BatchPlan plan;
     plan.inst_layout.resize(inst.size());
@@ -328,7 +334,8 @@ BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, 
         plan.inst_layout[(size_t)i] = {l.lanes, l.P};
         for (int64_t o = 0; o < inst[i].orbits; ++o) {
             const Cand c{i, (int32_t)o, inst[i].steps, l.lanes};
-            if (!l.team) packed[l.P].push_back(c);
+            if (l.solo) solo.push_back(c);
+            else if (!l.team) packed[l.P].push_back(c);
             else if (l.lanes == 128) team128[l.P].push_back(c);
             else team64[l.P].push_back(c);
         }
@@ -410,6 +417,15 @@ BatchPlan plan_batch(const std::vector<BatchInstance> &inst, double chain_frac, 
             }
             b0 = b1;
         }
+    }
+    for (const Cand &c : solo) {
+        BatchWarpTask wt{};
+        wt.p = 2;
+        wt.first = (int32_t)plan.items.size();
+        wt.count = 1;
+        wt.kmax = c.steps;
+        plan.items.push_back({c.instance, c.orbit});
+        warps.push_back({wt, (double)c.steps * batch_step_cost(2, false)});
     }
     std::stable_sort(warps.begin(), warps.end(), [](const CostedWarp &a, const CostedWarp &b) { return a.cost > b.cost; });
     for (size_t w = 0; w < warps.size(); w += 4) {

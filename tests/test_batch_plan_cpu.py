@@ -5,8 +5,8 @@ of one units-per-lane value side by side within 32 lanes, each on
 ceil(n / P) lanes, with step counts within a factor 1.2 of each other;
 teams hold one item on 64 or 128 lanes.  Without a chain limit nothing runs
 as a team; with the tightest limit every item takes the layout of the
-shortest chain for its n, a team with 2 units per lane (64 lanes up to
-n = 128, 128 lanes above)."""
+shortest chain for its n, 2 units per lane: a warp of its own up to n = 64,
+a 64-lane team up to 128, a 128-lane team above."""
 import math
 
 import numpy as np
@@ -49,7 +49,7 @@ def test_every_orbit_placed_once_and_warps_packed_within_32_lanes(frac):
     assert (plan["task"] >= 0).all() and (plan["task"] < plan["tasks"]).all()
     assert (lanes * upl >= n).all()
     packed = plan["slot"] <= 3
-    assert np.isin(upl[packed], [8, 4]).all()
+    assert np.isin(upl[packed], [8, 4, 2]).all()        # 2: an orbit alone on its warp
     assert (lanes[packed] == -(-n[packed] // upl[packed])).all()
     assert (lanes[packed] <= 32).all()
     team64 = (plan["slot"] == 4) | (plan["slot"] == 5)
@@ -64,6 +64,8 @@ def test_every_orbit_placed_once_and_warps_packed_within_32_lanes(frac):
             assert len(members) == 1                      # one item per team
             continue
         assert len({int(upl[g]) for g in members}) == 1   # one units-per-lane value per warp
+        if upl[members[0]] == 2:
+            assert len(members) == 1                      # a single-warp orbit has the warp to itself
         spans = sorted((int(plan["lane0"][g]), int(plan["lane0"][g] + lanes[g])) for g in members)
         assert spans[0][0] == 0 and spans[-1][1] <= 32
         for (a0, a1), (b0, _) in zip(spans, spans[1:]):
@@ -82,7 +84,10 @@ def test_chain_limit_extremes():
     assert (loose["slot"] <= 3).all() and (loose["lanes"] <= 32).all()
     tight = sdeb.sdeb_batch_plan(pbs, 1e-9, 152)
     for i, pb in enumerate(pbs):
-        want = (64, 2) if pb.n <= 128 else (128, 2)
+        if pb.n <= 64:
+            want = (-(-pb.n // 2), 2)    # a warp of its own
+        else:
+            want = (64, 2) if pb.n <= 128 else (128, 2)
         assert (tight["lanes"][i], tight["units_per_lane"][i]) == want, (pb.n, pb.steps)
 
 

@@ -2,8 +2,8 @@
 persistent, graph-launched kernel runs Kuramoto instances with different n,
 steps, dt, stride and orbit counts.  In FP64 every instance matches the
 oracle to 1e-12 under schedules that between them use every layout (packed
-warps with 8 and 4 units per lane, 64-lane teams with 4 and 2, 128-lane
-teams with 2).  FP32 runs the
+warps with 8 and 4 units per lane, orbits alone on a warp with 2, 64-lane
+teams with 4 and 2, 128-lane teams with 2).  FP32 runs the
 same template code and is held to 1e-4 on every instance over the
 horizon the single-problem path states, t <= 10 (each instance's step count
 is capped at 10 / dt).  An item's results do not depend on the items packed
@@ -73,7 +73,7 @@ def _layout_kind(lanes, units_per_lane):
     return ("packed" if lanes <= 32 else "team%d" % lanes, units_per_lane)
 
 
-ALL_KINDS = {("packed", 8), ("packed", 4), ("team64", 4), ("team64", 2), ("team128", 2)}
+ALL_KINDS = {("packed", 8), ("packed", 4), ("packed", 2), ("team64", 4), ("team64", 2), ("team128", 2)}
 
 
 def _schedules_covering_every_layout(b, specs):
