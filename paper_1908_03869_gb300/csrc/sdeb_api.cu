@@ -551,7 +551,7 @@ sdeb_status autotune_batch(sdeb_ctx *c, cudaStream_t s) {
     float best_ms = 1e30f;
     bool first = true;
     const int cap = c->grid_cap;
-    for (double frac : {0.125, 0.25, 0.5, 1.0, 2.0})
+    for (double frac : {0.125, 0.18, 0.25, 0.35, 0.5, 0.7, 1.0, 2.0})
       for (int per_sm : {2, 3, 4, 5}) {
         if (e != cudaSuccess) break;
         c->grid_cap = std::min(cap, per_sm * c->num_sms);
