@@ -16,6 +16,19 @@ namespace sdeb {
 
 namespace {
 
+// Reducers whose FP32 sums are 32-bit fixed point (multiples of 2^-22) mark
+// themselves with kScaled22: they take partial sums already scaled by 2^22
+// and return the integer totals unscaled, and the item's model carries the
+// two powers of two instead (its unit weights times 2^22, its (K/n) dt times
+// 2^-22).  Scaling by a power of two commutes with every rounding here (no
+// value comes near the subnormal range unless (K/n) dt is below 2^-104), so
+// the partials, totals and drift products are the same bits as with the
+// scalings in the reducer, two multiplies fewer per sum and step.
+template <class R, class = void>
+struct Scaled22 : std::false_type {};
+template <class R>
+struct Scaled22<R, std::void_t<decltype(R::kScaled22)>> : std::bool_constant<R::kScaled22> {};
+
 template <typename Real, int P>
 __device__ __forceinline__ void flag_nonfinite(uint8_t *flag, const Real (&x)[1][P], int u0, int units) {
     bool bad = false;
@@ -50,6 +63,11 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const BatchItem it,
     M model;
     model.load(static_cast<const Real *>(a.params) + in.p_off + (int64_t)it.orbit * in.param_stride, u0, units,
                (Real)in.dt, (Real)sqrt(in.dt));
+    if constexpr (Scaled22<RED>::value) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) model.live[i] *= 0x1p22f;
+        model.kn_dt *= 0x1p-22f;
+    }
     Real *xrow = static_cast<Real *>(a.x) + in.x_off + (int64_t)it.orbit * n;
     float *crow = kKahan ? a.comp + in.x_off + (int64_t)it.orbit * n : nullptr;
     Real x[1][P], cp[1][P];
@@ -204,11 +222,11 @@ struct SoloWarpSum {
 
 template <>
 struct SoloWarpSum<float> {
+    static constexpr bool kScaled22 = true;   // partials arrive times 2^22, totals leave unscaled
     template <int NR>
     __device__ __forceinline__ void operator()(float (&r)[NR]) const {
 #pragma unroll
-        for (int q = 0; q < NR; ++q)
-            r[q] = __int2float_rn(__reduce_add_sync(0xffffffffu, __float2int_rn(r[q] * 0x1p22f))) * 0x1p-22f;
+        for (int q = 0; q < NR; ++q) r[q] = __int2float_rn(__reduce_add_sync(0xffffffffu, __float2int_rn(r[q])));
     }
 };
 
@@ -265,32 +283,55 @@ struct NamedTeamSum {
 // the team's warps through shared memory.  Integer addition is exact, so the
 // totals are the same bits in every lane and in any order, and the rounding
 // (at most 2^-23 per lane) is of the order of the FP32 butterfly's.
+// With two sums the warp's pair goes to shared memory as one 8-byte store
+// and the team's slots come back as 16-byte loads (the slots are 16-byte
+// aligned).  The partials arrive scaled by 2^22 (kScaled22).
 template <int NW, int BAR>
 struct NamedTeamSum<NW, BAR, float> {
-    float *buf;  // [2][NW][2] words in shared memory, used as int
+    static constexpr bool kScaled22 = true;
+    float *buf;  // [2][NW][2] words in shared memory, used as int; 16-byte aligned
     int flip;
     int warp0;
     template <int NR>
     __device__ __forceinline__ void operator()(float (&r)[NR]) {
         static_assert(NR <= 2, "two sums at most");
+        constexpr bool kVec = NR == 2 && (NW == 2 || NW == 4);
         const int warp = (threadIdx.x >> 5) - warp0, lane = threadIdx.x & 31;
         int *slot = reinterpret_cast<int *>(buf) + flip * NW * 2;
+        int ws[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            const int ws = __reduce_add_sync(0xffffffffu, __float2int_rn(r[q] * 0x1p22f));
-            if (lane == 0) slot[warp * 2 + q] = ws;
+        for (int q = 0; q < NR; ++q) ws[q] = __reduce_add_sync(0xffffffffu, __float2int_rn(r[q]));
+        if (lane == 0) {
+            if constexpr (kVec) {
+                *reinterpret_cast<int2 *>(slot + warp * 2) = make_int2(ws[0], ws[NR - 1]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NR; ++q) slot[warp * 2 + q] = ws[q];
+            }
         }
         if constexpr (BAR == 0) {
             __syncthreads();
         } else {
             asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NW * 32) : "memory");
         }
+        if constexpr (kVec) {
+            const int4 u = reinterpret_cast<const int4 *>(slot)[0];
+            int t0 = u.x + u.z, t1 = u.y + u.w;
+            if constexpr (NW == 4) {
+                const int4 v = reinterpret_cast<const int4 *>(slot)[1];
+                t0 += v.x + v.z;
+                t1 += v.y + v.w;
+            }
+            r[0] = __int2float_rn(t0);
+            r[NR - 1] = __int2float_rn(t1);
+        } else {
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
-            int t = slot[q];
+            for (int q = 0; q < NR; ++q) {
+                int t = slot[q];
 #pragma unroll
-            for (int w = 1; w < NW; ++w) t += slot[w * 2 + q];
-            r[q] = __int2float_rn(t) * 0x1p-22f;
+                for (int w = 1; w < NW; ++w) t += slot[w * 2 + q];
+                r[q] = __int2float_rn(t);
+            }
         }
         flip ^= 1;
     }
@@ -314,7 +355,7 @@ __device__ __forceinline__ void run_team(const BatchArgs &a, int32_t item, Real 
 template <typename Real>
 __global__ void __launch_bounds__(kBatchBlock, 5) em_batch_kernel(const BatchArgs a) {
     __shared__ int s_task;
-    __shared__ Real s_red[2][2 * 4 * 2];
+    __shared__ __align__(16) Real s_red[2][2 * 4 * 2];
     for (;;) {
         if (threadIdx.x == 0) s_task = atomicAdd(a.head, 1);
         __syncthreads();
