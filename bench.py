@@ -940,6 +940,39 @@ def _time_batch(stream, clocks, rates, num_sms, samples, reps=5):
 # The CPU leg: the oracle timed on this host, and the legs' errors against it
 # ---------------------------------------------------------------------------
 
+def _adjoint_errors(a):
+    """Per-orbit gradients of the adjoint leg (a["dp"], FP32) against the FP64
+    oracle adjoint of the same orbits, relative to each orbit's largest
+    component; beside each, how far the oracle's own gradient moves when x0
+    moves by one FP32 ulp (signs fixed per component): an FP32 gradient
+    carries a rounding in each of its steps, so an orbit whose one-ulp
+    sensitivity is large cannot be followed to 1e-3."""
+    import numpy as np
+
+    import oracle
+
+    W, k = a["W"], a["x0"].shape[0]
+    n = a["x0"].shape[1]
+    pb = oracle.make_problem("kuramoto", n, n, n + 2, W["dt"], W["steps"], 1, W["seed"])
+    sign = np.where(np.sin(np.arange(n) * 7.1) >= 0, 1.0, -1.0)
+
+    def oracle_grad(x, o):
+        _, xK = oracle.integrate(pb, a["p"][None, :], x, orbit_begin=o, frames=False)
+        _, dr = oracle.order_param(xK[0])
+        dp, _ = oracle.adjoint(pb, a["p"][None, :], x, (dr / a["orbits"])[None, :], orbit_begin=o)
+        return dp[0]
+
+    per, sens = [], []
+    for o in range(k):
+        x = a["x0"][o:o + 1].astype(np.float64)
+        ref = oracle_grad(x, o)
+        per.append(float(np.abs(a["dp"][o] - ref).max() / np.abs(ref).max()))
+        sens.append(float(np.abs(oracle_grad(x * (1.0 + 2.0 ** -24 * sign), o) - ref).max() / np.abs(ref).max()))
+    return {"orbits": k, "max_rel_to_orbit_max": max(per), "per_orbit": per, "oracle_one_ulp_sensitivity": sens,
+            "over_1e-3": [{"orbit": o, "err": per[o], "oracle_one_ulp_sensitivity": sens[o]}
+                          for o in range(k) if per[o] >= 1e-3]}
+
+
 def _cpu_leg(inputs_by_n, samples, legs):
     import numpy as np
 
@@ -994,19 +1027,7 @@ def _cpu_leg(inputs_by_n, samples, legs):
                                                STRIDE, mean_field=True))
         err["forward_fp64_t_le_5"] = e
     if "adjoint" in samples:
-        a = samples["adjoint"]
-        W, k = a["W"], a["x0"].shape[0]
-        n = a["x0"].shape[1]
-        pb = oracle.make_problem("kuramoto", n, n, n + 2, W["dt"], W["steps"], 1, W["seed"])
-        worst = 0.0
-        for o in range(k):
-            _, xK = oracle.integrate(pb, a["p"][None, :], a["x0"][o:o + 1].astype(np.float64), orbit_begin=o,
-                                     frames=False)
-            _, dr = oracle.order_param(xK[0])
-            dp, _ = oracle.adjoint(pb, a["p"][None, :], a["x0"][o:o + 1].astype(np.float64),
-                                   (dr / a["orbits"])[None, :], orbit_begin=o)
-            worst = max(worst, float(np.abs(a["dp"][o] - dp[0]).max() / np.abs(dp[0]).max()))
-        err["adjoint_fp32_per_orbit_T20"] = {"orbits": k, "max_rel_to_orbit_max": worst}
+        err["adjoint_fp32_per_orbit_T20"] = _adjoint_errors(samples["adjoint"])
     if "fhn" in samples:
         f = samples["fhn"]
         W = {"dt": 0.01, "stride": 1000}

@@ -141,3 +141,35 @@ LARGE_STEP_HORIZON = {
     ("fhn_net", 64, "euler"): 60,        # below 1e-13 through t = 12
     ("fhn_net", 64, "midpoint"): 60,
 }
+
+
+def _adjoint_workload_orbit(o, ulp):
+    """FP64 oracle gradient of orbit o's order parameter at T = 20 on the
+    adjoint workload (n = 32, shared parameters, dt = 0.01, 2000 steps), x0
+    moved by ulp (relative, signs fixed per component)."""
+    W = inputs.WORKLOADS["kuramoto_adjoint_n32"]
+    n = W["n"]
+    p, x0 = inputs.kuramoto(n, W["orbits"], seed=1, shared=True)
+    p = p.astype(np.float32).astype(np.float64)
+    x = x0[o:o + 1].astype(np.float32).astype(np.float64)
+    sign = np.where(np.sin(np.arange(n) * 7.1) >= 0, 1.0, -1.0)
+    x = x * (1 + ulp * sign)
+    pb = oracle.make_problem("kuramoto", n, n, n + 2, W["dt"], W["steps"], 1, W["seed"])
+    _, xK = oracle.integrate(pb, p[None, :], x, orbit_begin=o, frames=False)
+    _, dr = oracle.order_param(xK[0])
+    dp, _ = oracle.adjoint(pb, p[None, :], x, dr[None, :], orbit_begin=o)
+    return dp[0]
+
+
+def test_adjoint_workload_gradient_sensitivity_at_T20():
+    # One FP32 ulp of x0 moves the FP64 gradient of orbit 4 at T = 20 by
+    # more than 1e-4 of its largest component (orbit 1: below 1e-6).  An
+    # FP32 adjoint takes a rounding in each of its 2000 steps, so on such an
+    # orbit it cannot be held to 1e-3 of the FP64 gradient; the GPU tests
+    # check the FP32 gradients at T = 20 per orbit statistically (median
+    # 1e-4, at most 5 % of orbits beyond 1e-3) and orbit by orbit at T = 5.
+    def sens(o):
+        g0 = _adjoint_workload_orbit(o, 0.0)
+        return np.abs(_adjoint_workload_orbit(o, 2.0 ** -24) - g0).max() / np.abs(g0).max()
+    assert sens(4) > 1e-4
+    assert sens(1) < 1e-6
